@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the PSD solver on GB300.
+
+Workload: the 3D 256^3 sixth-order (square phase field crystal shaped)
+problem, p = 4, lambda = 1, s = 0.05, eps = 0.1 on (0, 2 pi)^3, f and g
+seeded smooth random Fourier fields (32 modes, |k| <= 16), u0 = mean(g),
+solved to ||r||_2 < 1e-10.  One step = one complete solve from u0.
+
+value = dof-iterations/s of the mixed-precision path (FP32 inner PSD with
+FP64 reductions and outer FP64 residual correction), counting inner FP32
+iterations and outer FP64 residual sweeps; the plain FP64 GPU path is timed
+beside it.  Inputs are resident in HBM when the timed region starts; every
+field (134 MB in FP64) is larger than L2, so no extra L2 flush is done.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PSD dof-iter/s & time-to-1e-10 residual, 3D 256³, mixed vs FP64, GB300"
+UNIT = "dof-iter/s"
+TOL = 1e-10
+SAMPLE_N = 64          # grid of the CPU oracle sample (same workload family)
+SAMPLE_ITERS = 2       # PSD iterations per oracle sample
+
+
+def workload_config(n):
+    return {"workload": f"3D {n}^3 sixth-order PSD (SPFC-shaped: p=4, lambda=1, s=0.05, eps=0.1), "
+                        f"u0=mean(g), solve to ||r||_2<1e-10; mixed FP32/FP64 vs plain FP64",
+            "grid": [n, n, n], "order": 6, "tol": TOL,
+            "l2_flush": "none needed: every field (134 MB FP64 / 67 MB FP32) exceeds the 129 MB L2 "
+                        "or is streamed once per kernel"}
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# Algorithmic bytes per cell per launch of each kernel class on the
+# sixth-order path (reads + writes of whole fields, in the class precision).
+def algorithmic_bytes_per_cell(cls, order):
+    w = 8 if cls.endswith("fp64") else 4
+    table = {
+        "residual": 6 if cls.endswith("fp32") else 5,   # inner: delta, d, R, ubase in; delta', r out
+        "dht_rows": 2, "dht_cols": 2,
+        "mid": 6 if order == 6 else 2,                   # W, zeta, dspec in and out
+        "linesearch": 3 if cls.endswith("fp32") else 2,  # delta, ubase, d  /  u, d
+    }
+    base = cls.rsplit("_", 1)[0]
+    return table.get(base, 0) * w
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1607_01475_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(cls, n_cells):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        data = json.load(open(path))
+    except Exception:
+        return None
+    if data.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    ent = data.get("kernels", {}).get(cls)
+    if not ent:
+        return None
+    return ent["dram_bytes_per_cell"] * n_cells
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------ oracle sample
+
+def oracle_sample(iters=SAMPLE_ITERS, n=SAMPLE_N):
+    """Time the CPU oracle as it stands on a bounded sample of the workload:
+    `iters` PSD iterations of the same sixth-order problem on an n^3 grid."""
+    from oracle import psd_oracle as O
+    from paper_1607_01475_gb300 import synthetic
+    wl = synthetic.workload_spfc((n, n, n))
+    P = O.Problem(6, wl["L"] / n, wl["p"], wl["s"], wl["eps"], wl["lam"])
+    t0 = time.perf_counter()
+    O.psd_solve(P, wl["f"], wl["u0"], g=wl["g"], tol=0.0, kmax=iters)
+    dt = time.perf_counter() - t0
+    return n ** 3 * iters / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample()
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt = oracle_sample()
+        vals.append(v)
+        times.append(dt)
+    value = statistics.median(vals)
+    sample = (f"{SAMPLE_ITERS} PSD iterations of the same sixth-order problem (same parameters and "
+              f"field recipe) on a {SAMPLE_N}^3 grid per step; numpy FP64, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.median(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args.n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1607_01475_gb300 import PSD_FP64, PSD_MIXED, Solver, synthetic
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    shape = (n, n, n)
+    wl = synthetic.workload_spfc(shape)
+    h = wl["L"] / n
+    N = n ** 3
+    f_d = torch.from_numpy(wl["f"]).cuda()
+    g_d = torch.from_numpy(wl["g"]).cuda()
+    u0_d = torch.from_numpy(wl["u0"]).cuda()
+    u_d = torch.empty_like(u0_d)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(solver, steps, warmup, profile=False):
+        for _ in range(warmup):
+            u_d.copy_(u0_d)
+            solver.solve(f_d, u_d, g_d)
+        barrier()
+        if profile:
+            solver.profile(True)
+        infos = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            u_d.copy_(u0_d)
+            infos.append(solver.solve(f_d, u_d, g_d))
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof = solver.profile_read() if profile else None
+        if profile:
+            solver.profile(False)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, prof
+
+    # -------- mixed precision (headline)
+    mixed = Solver(6, shape, h, wl["p"], wl["s"], wl["eps"], wl["lam"], precision=PSD_MIXED, tol=TOL,
+                   max_iter=20000, max_outer=30)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_mixed, infos_mixed, prof = timed(mixed, args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    iters_mixed = sum(i["iters"] + i["outer_iters"] for i in infos_mixed)
+    value = world * N * iters_mixed / (ms_mixed / 1000.0)
+    assert all(i["status"] == 0 for i in infos_mixed), infos_mixed
+
+    # -------- plain FP64
+    fp64 = Solver(6, shape, h, wl["p"], wl["s"], wl["eps"], wl["lam"], precision=PSD_FP64, tol=TOL,
+                  max_iter=20000)
+    steps64 = max(1, args.steps)
+    ms64, infos64, _ = timed(fp64, steps64, max(1, min(args.warmup, 3)))
+    iters64 = sum(i["iters"] for i in infos64)
+    value64 = world * N * iters64 / (ms64 / 1000.0)
+
+    # -------- roofline of the dominant kernel of the mixed path
+    peaks, peak_src = load_peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    tot_ms, launches, eff_ms, eff_n = prof[dom]
+    avg_ms = eff_ms / max(eff_n, 1)
+    bpc = algorithmic_bytes_per_cell(dom, 6)
+    total_launches = sum(v[1] for v in prof.values())
+    share = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-12), 4) for k, v in prof.items() if v[1]}
+    if dom.endswith("fp32") or bpc and not dom.endswith("fp64"):
+        achieved = bpc * N / (avg_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom, N),
+                "kernel": dom, "algorithmic_bytes_per_launch": bpc * N,
+                "avg_launch_ms": avg_ms, "launches": eff_n, "peak_source": f"{peak_src} hbm_gbs"}
+    else:
+        achieved = bpc * N / (avg_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom, N),
+                "kernel": dom, "algorithmic_bytes_per_launch": bpc * N, "avg_launch_ms": avg_ms,
+                "launches": eff_n, "peak_source": f"{peak_src} hbm_gbs",
+                "note": "FP64 kernel: bound by FP64 issue rate, HBM fraction reported for reference"}
+
+    # -------- end to end through the C ABI with host buffers
+    f_h = torch.from_numpy(wl["f"]).pin_memory()
+    g_h = torch.from_numpy(wl["g"]).pin_memory()
+    u0_h = torch.from_numpy(wl["u0"]).pin_memory()
+    out_h = torch.empty_like(u0_h).pin_memory()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters_e2e = 0
+    for _ in range(args.steps):
+        f_d.copy_(f_h, non_blocking=True)
+        g_d.copy_(g_h, non_blocking=True)
+        u_d.copy_(u0_h, non_blocking=True)
+        info = mixed.solve(f_d, u_d, g_d)
+        iters_e2e += info["iters"] + info["outer_iters"]
+        out_h.copy_(u_d, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": world * N * iters_e2e / (ms_e2e / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": N * 8,
+           "ms_per_step": ms_e2e / args.steps}
+
+    # -------- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt = oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{SAMPLE_ITERS} PSD iterations of the same sixth-order problem on a {SAMPLE_N}^3 "
+                         f"grid ({dt:.1f} s, numpy FP64, single thread)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": workload_config(n),
+            "time_to_tol_ms": {"mixed": ms_mixed / args.steps, "fp64": ms64 / steps64},
+            "iterations_per_solve": {"mixed_inner": infos_mixed[-1]["iters"],
+                                     "mixed_outer": infos_mixed[-1]["outer_iters"],
+                                     "fp64": infos64[-1]["iters"]},
+            "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / steps64,
+                     "res_l2": infos64[-1]["res_l2"]},
+            "res_l2": infos_mixed[-1]["res_l2"],
+            "speedup_time_to_tol_mixed_vs_fp64": (ms64 / steps64) / (ms_mixed / args.steps),
+            "roofline": roof, "kernel_time_share_mixed": share,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": total_launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

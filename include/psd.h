@@ -1,0 +1,167 @@
+/*
+ * psd.h -- C ABI of the GB300 (sm_103a) preconditioned steepest descent (PSD)
+ * solver for the periodic finite-difference regularized p-Laplacian problems
+ * of Feng, Salgado, Wang & Wise, arXiv:1607.01475.
+ *
+ * Problems (cell-centred periodic grid, spacing h, Sec. 5):
+ *   order 4 (Eq. "discrete-4th-order", Sec. 5.3):
+ *       N_h[u] := u - s grad_h^v.(|grad_h^v u|^{p-2} grad_h^v u) + s eps^2 Delta_h^2 u = f
+ *   order 6 (Sec. 5.4, operator form of Sec. 6.2 with gamma_0 = lambda):
+ *       u - Delta_h w = g,
+ *       s lambda u - s grad_h^v.(...) + s eps^2 Delta_h^2 u - w = f,
+ *     solved for u with mean(u) = mean(g) as N_h[u] := s lambda u - s grad.(..)
+ *       + s eps^2 Delta_h^2 u + T_h[u - g] = f on the mean-zero space,
+ *     T_h = -Delta_h^{-1}; then w = -T_h[u - g] + s lambda mean(g) - mean(f).
+ *
+ * The PSD step (Sec. 2.2, Sec. 6.1): d^k solves L_h d^k = r^k := f - N_h[u^k]
+ * with the constant-coefficient preconditioner L_h = I - s Delta_h +
+ * s eps^2 Delta_h^2 (order 4, Sec. 5.3) or s lambda I - s Delta_h +
+ * s eps^2 Delta_h^2 + T_h (order 6, Sec. 5.4); u^{k+1} = u^k + alpha_k d^k with
+ * alpha_k the unique root of q(alpha) = (N_h[u^k + alpha d^k] - f, d^k)_2
+ * (Eq. "eqn-search").  3D operators are the tensor extension of the 2D ones.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are DEVICE pointers to contiguous float64 grids laid out
+ *    [nz][ny][nx] (x fastest; 2D: [ny][nx], n[2] = 1).  The caller owns them.
+ *  - Work is enqueued on the stream given in psd_params.stream (NULL = the
+ *    legacy default stream).  Calls that return scalars to the host
+ *    (psd_residual, psd_solve, psd_adjoint) synchronise that stream before
+ *    returning; psd_precond_solve is asynchronous.
+ *  - Every call returns a psd_status; nothing aborts.  After an error,
+ *    psd_last_error() returns a one-line description.
+ *  - A handle is not thread safe: one host thread at a time.
+ */
+#ifndef PSD_H
+#define PSD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PSD_OK = 0,
+  PSD_ERR_INVALID = 1,     /* bad parameter, size or pointer                 */
+  PSD_ERR_NOMEM = 2,       /* device allocation failed                       */
+  PSD_ERR_CUDA = 3,        /* a CUDA runtime call failed                     */
+  PSD_ERR_NOCONV = 4,      /* max_iter / max_outer reached above tol         */
+  PSD_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                  */
+  PSD_ERR_UNSUPPORTED = 6, /* valid but not implemented combination          */
+  PSD_ERR_NONFINITE = 7    /* NaN/Inf met in a residual or step size         */
+} psd_status;
+
+enum { PSD_FP64 = 0, PSD_MIXED = 1 };
+
+typedef struct psd_params {
+  int order;        /* 4 or 6                                                  */
+  int dim;          /* 2 or 3                                                  */
+  int n[3];         /* cells per axis (x, y, z): powers of two in [8, 1024];
+                       n[2] = 1 in 2D                                          */
+  double h;         /* isotropic grid spacing (Sec. 5.1), h > 0                */
+  double p;         /* p >= 2 (Sec. 3.1; 3D requires p <= 6)                   */
+  double s;         /* s > 0                                                   */
+  double eps;       /* 0 < eps (the paper takes eps <= 1)                      */
+  double lambda;    /* lambda >= 0, order 6 only                               */
+  int precision;    /* PSD_FP64 or PSD_MIXED (FP32 inner PSD + FP64 outer
+                       residual correction)                                    */
+  double tol;       /* stop when ||r||_2 = (h^d sum r^2)^{1/2} < tol           */
+  int max_iter;     /* PSD iterations (mixed: total inner iterations)         */
+  int max_outer;    /* mixed mode: outer FP64 residual corrections             */
+  void* stream;     /* cudaStream_t                                            */
+} psd_params;
+
+typedef struct psd_info {
+  int iters;          /* PSD iterations (mixed: inner FP32 iterations)        */
+  int outer_iters;    /* mixed: FP64 outer residual evaluations               */
+  double res_l2;      /* final ||f - N_h[u]||_2 (order 6: mean-projected)     */
+  double res_linf;    /* final max |r| (order 4 FP64; -1 when not formed)     */
+  double last_alpha;  /* last step size                                       */
+  double wall_ms;     /* device time of the solve (CUDA events)               */
+  int status;         /* psd_status of the solve                              */
+} psd_info;
+
+typedef struct psd_context* psd_handle;
+
+/* Create a solver for one problem size and parameter set.  Validates every
+ * field (PSD_ERR_INVALID on a bad one), builds the transform tables and
+ * allocates the device workspace with cudaMalloc (PSD_ERR_NOMEM).  The
+ * workspace is owned by the handle and freed by psd_destroy.             */
+psd_status psd_create(const psd_params* params, psd_handle* out);
+
+/* Free the workspace and the handle (NULL is accepted).                  */
+psd_status psd_destroy(psd_handle h);
+
+/* Residual r = f - N_h[u] (order 6: P0[f - N_h[u]] with g required) as in
+ * Sec. 6.1 and 6.2.  r may be NULL; res_l2 / res_linf are host pointers
+ * (either may be NULL) receiving ||r||_2 and max|r|.  Always FP64.        */
+psd_status psd_residual(psd_handle h, const double* u, const double* f,
+                        const double* g, double* r, double* res_l2,
+                        double* res_linf);
+
+/* Search direction: solve L_h d = r by the FFT (Sec. 6; symbol of L_h from
+ * Sec. 5.3 / 5.4).  Order 6 returns the mean-zero solution for P0 r.
+ * r and d may alias.  Asynchronous on the handle's stream.  Always FP64.  */
+psd_status psd_precond_solve(psd_handle h, const double* r, double* d);
+
+/* PSD solve of N_h[u] = f (order 6: with g) from the initial guess in u; u
+ * is overwritten with the result.  w (order 6, may be NULL) receives
+ * w = -T_h[u - g] + s lambda mean(g) - mean(f).  info (host, may be NULL)
+ * receives the statistics.  Returns PSD_ERR_NOCONV if the tolerance was
+ * not met within the iteration limits (u then holds the last iterate).     */
+psd_status psd_solve(psd_handle h, const double* f, const double* g,
+                     double* u, double* w, psd_info* info);
+
+/* Record per-iteration step sizes alpha_k and residual norms ||r_k||_2 of
+ * subsequent psd_solve calls into host arrays of capacity cap (both may be
+ * NULL to stop recording).  res_hist[0] is ||r_0||.                        */
+psd_status psd_set_history(psd_handle h, double* alpha_hist, double* res_hist,
+                           int cap);
+
+/* FP32 residual of the stencil kernel (used by the mixed path), for tests:
+ * r = f - N_h[u] in float (order 6: the local part, without T_h).          */
+psd_status psd_residual_f32(psd_handle h, const float* u, const float* f,
+                            float* r);
+
+/* Kernel classes reported by psd_profile_read (index = class).            */
+enum {
+  PSD_PROF_RESIDUAL_FP64 = 0, PSD_PROF_RESIDUAL_FP32 = 1,
+  PSD_PROF_DHT_ROWS_FP64 = 2, PSD_PROF_DHT_ROWS_FP32 = 3,
+  PSD_PROF_DHT_COLS_FP64 = 4, PSD_PROF_DHT_COLS_FP32 = 5,
+  PSD_PROF_MID_FP64 = 6,      PSD_PROF_MID_FP32 = 7,
+  PSD_PROF_LINESEARCH_FP64 = 8, PSD_PROF_LINESEARCH_FP32 = 9,
+  PSD_PROF_OTHER = 10,
+  PSD_PROF_CLASSES = 11
+};
+
+/* Per-kernel timing (tracing).  While enabled, every kernel launch of this
+ * handle is bracketed by CUDA events on the handle's stream; the events
+ * cost a few microseconds of host time per launch and do not change the
+ * order of work.  psd_profile(h, 1) enables and clears the counters,
+ * psd_profile(h, 0) disables.                                              */
+psd_status psd_profile(psd_handle h, int enable);
+
+/* Accumulated device milliseconds and launch counts per kernel class since
+ * the last psd_profile(h, 1) (synchronises the stream).  Kernels launched
+ * after the stop flag is set return at once; the "effective" figures count
+ * only launches that ran longer than eff_us microseconds.  All arrays are
+ * host arrays of length n (n <= PSD_PROF_CLASSES); any may be NULL.        */
+psd_status psd_profile_read(psd_handle h, double* ms, long long* launches,
+                            double* eff_ms, long long* eff_launches,
+                            double eff_us, int n);
+
+/* Static name of a kernel class ("residual_fp64", ...), or NULL.           */
+const char* psd_profile_class_name(int k);
+
+/* Text of the last error on this handle (or of the last psd_create failure
+ * when h is NULL), copied into buf (always NUL-terminated).                */
+psd_status psd_last_error(psd_handle h, char* buf, size_t len);
+
+/* Static name of a status code.                                           */
+const char* psd_status_string(psd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSD_H */

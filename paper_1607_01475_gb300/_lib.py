@@ -1,0 +1,227 @@
+"""ctypes binding of libpsd.so: argument marshalling only.
+
+Tensors are torch CUDA tensors (float64, or float32 for psd_residual_f32),
+contiguous, shaped (ny, nx) in 2D or (nz, ny, nx) in 3D (x fastest).  Work is
+enqueued on torch's current CUDA stream unless a stream is given.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_NAME = "libpsd.so"
+
+PSD_FP64 = 0
+PSD_MIXED = 1
+
+_STATUS = {0: "PSD_OK", 1: "PSD_ERR_INVALID", 2: "PSD_ERR_NOMEM", 3: "PSD_ERR_CUDA",
+           4: "PSD_ERR_NOCONV", 5: "PSD_ERR_TIMEOUT", 6: "PSD_ERR_UNSUPPORTED",
+           7: "PSD_ERR_NONFINITE"}
+
+
+class PSDParams(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("h", ctypes.c_double), ("p", ctypes.c_double), ("s", ctypes.c_double),
+                ("eps", ctypes.c_double), ("lam", ctypes.c_double), ("precision", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class PSDInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("res_l2", ctypes.c_double),
+                ("res_linf", ctypes.c_double), ("last_alpha", ctypes.c_double),
+                ("wall_ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PSDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib_path():
+    return os.path.join(HERE, _LIB_NAME)
+
+
+def load_library(build_if_missing=True):
+    """Load libpsd.so (building it with nvcc if absent).  Raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path) and build_if_missing:
+        from . import build as _build
+        _build.build()
+    if not os.path.exists(path):
+        raise PSDError(3, f"{path} not found; build it with paper_1607_01475_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    P, H, D, F = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
+    lib.psd_create.argtypes = [ctypes.POINTER(PSDParams), ctypes.POINTER(ctypes.c_void_p)]
+    lib.psd_destroy.argtypes = [H]
+    lib.psd_residual.argtypes = [H, D, D, D, D, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.psd_precond_solve.argtypes = [H, D, D]
+    lib.psd_solve.argtypes = [H, D, D, D, D, ctypes.POINTER(PSDInfo)]
+    lib.psd_set_history.argtypes = [H, P, P, ctypes.c_int]
+    lib.psd_residual_f32.argtypes = [H, F, F, F]
+    lib.psd_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
+    lib.psd_profile.argtypes = [H, ctypes.c_int]
+    lib.psd_profile_read.argtypes = [H, P, P, P, P, ctypes.c_double, ctypes.c_int]
+    lib.psd_profile_class_name.argtypes = [ctypes.c_int]
+    lib.psd_profile_class_name.restype = ctypes.c_char_p
+    lib.psd_status_string.argtypes = [ctypes.c_int]
+    lib.psd_status_string.restype = ctypes.c_char_p
+    for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
+                 "psd_set_history", "psd_residual_f32", "psd_last_error", "psd_profile",
+                 "psd_profile_read"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def psd_status_string(status):
+    return load_library().psd_status_string(int(status)).decode()
+
+
+def _last_error(handle):
+    buf = ctypes.create_string_buffer(512)
+    load_library().psd_last_error(handle, buf, len(buf))
+    return buf.value.decode()
+
+
+def _check(status, handle, allow=()):
+    if status != 0 and status not in allow:
+        raise PSDError(status, _last_error(handle))
+    return status
+
+
+def _ptr(t, dtype_name="float64"):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != f"torch.{dtype_name}":
+        raise PSDError(1, f"expected a contiguous CUDA {dtype_name} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------ C-named calls
+
+def psd_create(order, shape, h, p, s, eps, lam=0.0, precision=PSD_FP64, tol=1e-10,
+               max_iter=10000, max_outer=20, stream=None):
+    """Create a solver handle for a grid of ``shape`` ((ny, nx) or (nz, ny, nx))."""
+    lib = load_library()
+    dim = len(shape)
+    n = (shape[-1], shape[-2], shape[0] if dim == 3 else 1)
+    prm = PSDParams(order=order, dim=dim, n=(ctypes.c_int * 3)(*n), h=h, p=p, s=s, eps=eps, lam=lam,
+                    precision=precision, tol=tol, max_iter=max_iter, max_outer=max_outer,
+                    stream=_stream_handle(stream) if stream is not False else None)
+    out = ctypes.c_void_p()
+    _check(lib.psd_create(ctypes.byref(prm), ctypes.byref(out)), None)
+    return out
+
+
+def psd_destroy(handle):
+    return load_library().psd_destroy(handle)
+
+
+def psd_residual(handle, u, f, g=None, r=None):
+    l2, linf = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().psd_residual(handle, _ptr(u), _ptr(f), _ptr(g), _ptr(r),
+                                       ctypes.byref(l2), ctypes.byref(linf)), handle)
+    return l2.value, linf.value
+
+
+def psd_precond_solve(handle, r, d):
+    _check(load_library().psd_precond_solve(handle, _ptr(r), _ptr(d)), handle)
+
+
+def psd_solve(handle, f, u, g=None, w=None, allow_noconv=False):
+    info = PSDInfo()
+    allow = (4,) if allow_noconv else ()
+    _check(load_library().psd_solve(handle, _ptr(f), _ptr(g), _ptr(u), _ptr(w), ctypes.byref(info)),
+           handle, allow)
+    return info.as_dict()
+
+
+def psd_residual_f32(handle, u, f, r):
+    _check(load_library().psd_residual_f32(handle, _ptr(u, "float32"), _ptr(f, "float32"),
+                                           _ptr(r, "float32")), handle)
+
+
+# ------------------------------------------------------------- convenience
+
+class Solver:
+    """Owns one handle.  ``shape`` is (ny, nx) or (nz, ny, nx)."""
+
+    def __init__(self, order, shape, h, p, s, eps, lam=0.0, precision=PSD_FP64, tol=1e-10,
+                 max_iter=10000, max_outer=20, stream=None):
+        self.shape = tuple(shape)
+        self.handle = psd_create(order, shape, h, p, s, eps, lam, precision, tol, max_iter,
+                                 max_outer, stream)
+        self._hist = None
+
+    def close(self):
+        if self.handle:
+            psd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def residual(self, u, f, g=None, r=None):
+        return psd_residual(self.handle, u, f, g, r)
+
+    def precond_solve(self, r, d):
+        psd_precond_solve(self.handle, r, d)
+
+    def residual_f32(self, u, f, r):
+        psd_residual_f32(self.handle, u, f, r)
+
+    def set_history(self, cap):
+        import numpy as np
+        if cap <= 0:
+            self._hist = None
+            _check(load_library().psd_set_history(self.handle, None, None, 0), self.handle)
+            return
+        a = np.full(cap, np.nan)
+        r = np.full(cap, np.nan)
+        _check(load_library().psd_set_history(self.handle, a.ctypes.data_as(ctypes.c_void_p),
+                                              r.ctypes.data_as(ctypes.c_void_p), cap), self.handle)
+        self._hist = (a, r)
+
+    def history(self):
+        return self._hist
+
+    def solve(self, f, u, g=None, w=None, allow_noconv=False):
+        return psd_solve(self.handle, f, u, g, w, allow_noconv)
+
+    def profile(self, enable=True):
+        _check(load_library().psd_profile(self.handle, 1 if enable else 0), self.handle)
+
+    def profile_read(self, eff_us=8.0):
+        """{class name: (ms, launches, effective ms, effective launches)}."""
+        import numpy as np
+        n = 11
+        ms = np.zeros(n)
+        cnt = np.zeros(n, dtype=np.int64)
+        ems = np.zeros(n)
+        ecnt = np.zeros(n, dtype=np.int64)
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        lib = load_library()
+        _check(lib.psd_profile_read(self.handle, ptr(ms), ptr(cnt), ptr(ems), ptr(ecnt), eff_us, n),
+               self.handle)
+        return {lib.psd_profile_class_name(k).decode(): (float(ms[k]), int(cnt[k]), float(ems[k]), int(ecnt[k]))
+                for k in range(n)}

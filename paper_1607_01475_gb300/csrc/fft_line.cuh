@@ -1,0 +1,170 @@
+// Line FFTs in shared memory and the discrete Hartley transform (DHT) built
+// on them.
+//
+// Why the DHT: the preconditioner L_h, the Poisson inverse T_h and Delta_h
+// all have Fourier symbols that depend on sin^2(pi k_a / n_a) only, i.e. are
+// real and even in each wavenumber separately.  The separable Hartley
+// transform H = H_x H_y H_z (kernel cas(2 pi j k / n) = cos + sin per axis)
+// therefore diagonalises them with the same symbols, maps real grids to real
+// grids of the same shape, and is its own inverse up to 1/N.  A 1D DHT of
+// two real lines x, y is read off one complex FFT of z = x + i y:
+//   with Z_k = A + iB and Z_{n-k} = C + iD,
+//   H[x]_k = (A - B + C + D)/2,  H[y]_k = (A + B - C + D)/2.
+//
+// The complex FFT is a Stockham autosort FFT: a line of N points is handled
+// by a team of TS = N/R threads holding R points each in registers; each pass
+// of radix RP (RP | R) does R/RP butterflies per thread and exchanges data
+// through shared memory.  Pass with Ns = product of earlier radices:
+// butterfly j' reads x[j' + r N/RP], twiddles by W_N^{(j' mod Ns) r N/(Ns RP)},
+// does an RP-point DFT and writes y[(j'/Ns) Ns RP + (j' mod Ns) + r Ns].
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace psd {
+
+// cos(2 pi m / 16), the 16th roots of unity (exact values of cos(pi/8),
+// sin(pi/8) and sqrt(2)/2).
+__host__ __device__ constexpr double cos16(int m) {
+  return (m & 15) == 0 ? 1.0
+       : (m & 15) == 1 ? 0.92387953251128675613
+       : (m & 15) == 2 ? 0.70710678118654752440
+       : (m & 15) == 3 ? 0.38268343236508977173
+       : (m & 15) == 4 ? 0.0
+       : (m & 15) == 5 ? -0.38268343236508977173
+       : (m & 15) == 6 ? -0.70710678118654752440
+       : (m & 15) == 7 ? -0.92387953251128675613
+       : (m & 15) == 8 ? -1.0
+       : (m & 15) == 9 ? -0.92387953251128675613
+       : (m & 15) == 10 ? -0.70710678118654752440
+       : (m & 15) == 11 ? -0.38268343236508977173
+       : (m & 15) == 12 ? 0.0
+       : (m & 15) == 13 ? 0.38268343236508977173
+       : (m & 15) == 14 ? 0.70710678118654752440
+                        : 0.92387953251128675613;
+}
+__host__ __device__ constexpr double sin16(int m) { return cos16(m - 4); }
+
+// In-register DFT of size R (R | 16): radix-2 decimation in time, in-order
+// input and output.  X_k = sum_j x_j exp(-2 pi i j k / R).
+template <int R>
+struct DFT {
+  template <typename T>
+  __device__ __forceinline__ static void run(T (&re)[R], T (&im)[R]) {
+    T er[R / 2], ei[R / 2], orr[R / 2], oi[R / 2];
+#pragma unroll
+    for (int j = 0; j < R / 2; ++j) {
+      er[j] = re[2 * j];
+      ei[j] = im[2 * j];
+      orr[j] = re[2 * j + 1];
+      oi[j] = im[2 * j + 1];
+    }
+    DFT<R / 2>::run(er, ei);
+    DFT<R / 2>::run(orr, oi);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      T tr, ti;
+      if (k == 0) {
+        tr = orr[k];
+        ti = oi[k];
+      } else if (4 * k == R) {  // W = -i
+        tr = oi[k];
+        ti = -orr[k];
+      } else {  // W = c - i sn
+        const T c = (T)cos16(k * 16 / R), sn = (T)sin16(k * 16 / R);
+        tr = orr[k] * c + oi[k] * sn;
+        ti = oi[k] * c - orr[k] * sn;
+      }
+      re[k] = er[k] + tr;
+      im[k] = ei[k] + ti;
+      re[k + R / 2] = er[k] - tr;
+      im[k + R / 2] = ei[k] - ti;
+    }
+  }
+};
+template <>
+struct DFT<1> {
+  template <typename T>
+  __device__ __forceinline__ static void run(T (&)[1], T (&)[1]) {}
+};
+
+// Complex FFT of one line of N points by a team of TS threads (team index
+// j).  Input: registers vr/vi holding x[j + q TS], q < R.  Output: the
+// transform in natural order in sr/si (shared memory, length N), visible to
+// the whole block on return.  Every thread of the block must call this
+// (it contains __syncthreads).  twc/tws: cos/sin(2 pi t / N), t < N.
+template <typename T, int N>
+struct LineFFT {
+  static constexpr int R = N < 16 ? N : 16;
+  static constexpr int TS = N / R;
+
+  template <int NS>
+  __device__ __forceinline__ static void pass(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si,
+                                              const T* __restrict__ twc, const T* __restrict__ tws) {
+    constexpr int RP = (N / NS >= R) ? R : N / NS;
+    constexpr int M = R / RP;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const int jp = j + b * TS;
+      const int jm = jp & (NS - 1);
+      T xr[RP], xi[RP];
+#pragma unroll
+      for (int r = 0; r < RP; ++r) {
+        xr[r] = vr[b + r * M];
+        xi[r] = vi[b + r * M];
+      }
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < RP; ++r) {
+          const int t = jm * r * (N / (NS * RP));
+          const T c = __ldg(twc + t), sn = __ldg(tws + t);
+          const T a = xr[r], bb = xi[r];
+          xr[r] = a * c + bb * sn;
+          xi[r] = bb * c - a * sn;
+        }
+      }
+      DFT<RP>::run(xr, xi);
+      const int base = (jp / NS) * NS * RP + jm;
+#pragma unroll
+      for (int r = 0; r < RP; ++r) {
+        sr[base + r * NS] = xr[r];
+        si[base + r * NS] = xi[r];
+      }
+    }
+  }
+
+  template <int NS>
+  __device__ __forceinline__ static void rest(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si,
+                                              const T* __restrict__ twc, const T* __restrict__ tws) {
+    if constexpr (NS < N) {
+      constexpr int RP = (N / NS >= R) ? R : N / NS;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        vr[q] = sr[j + q * TS];
+        vi[q] = si[j + q * TS];
+      }
+      __syncthreads();
+      pass<NS>(vr, vi, j, sr, si, twc, tws);
+      rest<NS * RP>(vr, vi, j, sr, si, twc, tws);
+    }
+  }
+
+  __device__ __forceinline__ static void run(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si,
+                                             const T* __restrict__ twc, const T* __restrict__ tws) {
+    pass<1>(vr, vi, j, sr, si, twc, tws);
+    rest<R>(vr, vi, j, sr, si, twc, tws);
+    __syncthreads();
+  }
+};
+
+// Hartley outputs of the two real lines packed in a complex spectrum.
+template <typename T>
+__device__ __forceinline__ void dht_split(const T* sr, const T* si, int k, int N, T& h1, T& h2) {
+  const int k2 = (N - k) & (N - 1);
+  const T A = sr[k], B = si[k], C = sr[k2], D = si[k2];
+  h1 = T(0.5) * ((A - B) + (C + D));
+  h2 = T(0.5) * ((A + B) - (C - D));
+}
+
+}  // namespace psd

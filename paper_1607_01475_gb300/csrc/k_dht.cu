@@ -1,0 +1,462 @@
+// Discrete Hartley transform passes of the FFT preconditioner (Sec. 6: the
+// search-direction equation L_h d = r is solved with the FFT), and the middle
+// pass that divides by the symbol of L_h (Sec. 5.3, 5.4) and forms the
+// Parseval sums the line search needs.
+#include <cmath>
+
+#include "fft_line.cuh"
+#include "kernels.h"
+
+namespace psd {
+namespace {
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+constexpr int PAD = 1;
+constexpr int kThreads = 256;
+constexpr size_t kMaxSmem = 96 * 1024;
+
+// -------------------------------------------------------------- x (rows)
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads)
+    k_dht_rows(const T* src, T* dst, int nrows, T scale, const int* done, const T* __restrict__ twc,
+               const T* __restrict__ tws) {
+  using F = LineFFT<T, N>;
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int pairs = blockDim.x / F::TS;
+  const int p = tid / F::TS, j = tid - p * F::TS;
+  const int row0 = 2 * (blockIdx.x * pairs + p);
+  const bool valid = row0 < nrows;
+  T* sr = sm + (size_t)p * 2 * (N + PAD);
+  T* si = sr + (N + PAD);
+  T vr[F::R], vi[F::R];
+  const T* s0 = src + (size_t)row0 * N;
+#pragma unroll
+  for (int q = 0; q < F::R; ++q) {
+    vr[q] = valid ? s0[j + q * F::TS] : T(0);
+    vi[q] = valid ? s0[N + j + q * F::TS] : T(0);
+  }
+  F::run(vr, vi, j, sr, si, twc, tws);
+  if (valid) {
+    T* d0 = dst + (size_t)row0 * N;
+#pragma unroll
+    for (int q = 0; q < F::R; ++q) {
+      const int k = j + q * F::TS;
+      T h1, h2;
+      dht_split(sr, si, k, N, h1, h2);
+      d0[k] = h1 * scale;
+      d0[N + k] = h2 * scale;
+    }
+  }
+}
+
+// ------------------------------------------------------ strided lines (y, z)
+// Block: `pairs` pairs of adjacent x-columns (x, x+1) packed as re/im, lines
+// along the strided axis; thread (p, j) = (tid % pairs, tid / pairs) so that a
+// warp reads whole row segments.
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads)
+    k_dht_cols(T* data, size_t line_stride, size_t outer_stride, T scale, const int* done,
+               const T* __restrict__ twc, const T* __restrict__ tws) {
+  using F = LineFFT<T, N>;
+  using V = typename Vec2<T>::type;
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int pairs = blockDim.x / F::TS;
+  const int p = tid % pairs, j = tid / pairs;
+  const size_t base = (size_t)blockIdx.y * outer_stride + (size_t)blockIdx.x * 2 * pairs + 2 * p;
+  T* sr = sm + (size_t)p * 2 * (N + PAD);
+  T* si = sr + (N + PAD);
+  T vr[F::R], vi[F::R];
+#pragma unroll
+  for (int q = 0; q < F::R; ++q) {
+    const V v = *reinterpret_cast<const V*>(data + base + (size_t)(j + q * F::TS) * line_stride);
+    vr[q] = v.x;
+    vi[q] = v.y;
+  }
+  F::run(vr, vi, j, sr, si, twc, tws);
+#pragma unroll
+  for (int q = 0; q < F::R; ++q) {
+    const int k = j + q * F::TS;
+    T h1, h2;
+    dht_split(sr, si, k, N, h1, h2);
+    V o;
+    o.x = h1 * scale;
+    o.y = h2 * scale;
+    *reinterpret_cast<V*>(data + base + (size_t)k * line_stride) = o;
+  }
+}
+
+// ------------------------------------------------------------- middle pass
+template <typename T, int N, int ORDER>
+__global__ void __launch_bounds__(kThreads)
+    k_mid(T* data, size_t line_stride, size_t outer_stride, KParams kp, Ctrl* ctrl, double* partials,
+          T* zeta, T* dspec, const T* __restrict__ symx, const T* __restrict__ symo,
+          const T* __restrict__ syml, const T* __restrict__ twc, const T* __restrict__ tws) {
+  using F = LineFFT<T, N>;
+  using V = typename Vec2<T>::type;
+  if (ctrl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ double sred[32 * 5];
+  __shared__ int sflag;
+  const int tid = threadIdx.x;
+  const int pairs = blockDim.x / F::TS;
+  const int p = tid % pairs, j = tid / pairs;
+  const int x = blockIdx.x * 2 * pairs + 2 * p;
+  const size_t base = (size_t)blockIdx.y * outer_stride + x;
+  T* sr = sm + (size_t)p * 2 * (N + PAD);
+  T* si = sr + (N + PAD);
+  T vr[F::R], vi[F::R];
+#pragma unroll
+  for (int q = 0; q < F::R; ++q) {
+    const V v = *reinterpret_cast<const V*>(data + base + (size_t)(j + q * F::TS) * line_stride);
+    vr[q] = v.x;
+    vi[q] = v.y;
+  }
+  F::run(vr, vi, j, sr, si, twc, tws);
+
+  const T mo = (symo != nullptr) ? symo[blockIdx.y] : T(0);
+  const T mxa = symx[x] + mo, mxb = symx[x + 1] + mo;
+  const T s = (T)kp.s, se2 = (T)(kp.s * kp.eps2), sl = (T)(kp.s * kp.lam);
+  const T alpha_prev = (ORDER == 6) ? (T)ctrl->alpha : T(0);
+  T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < F::R; ++q) {
+    const int k = j + q * F::TS;
+    T h[2];
+    dht_split(sr, si, k, N, h[0], h[1]);
+    const T ml = syml[k];
+    T dv[2];
+    if (ORDER == 4) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T mu = (c ? mxb : mxa) + ml;
+        const T L = T(1) + s * mu + se2 * mu * mu;
+        const T dd = h[c] / L;
+        dv[c] = dd;
+        acc[0] += h[c] * dd;
+        acc[1] += dd * dd;
+        acc[2] += (mu * dd) * (mu * dd);
+      }
+    } else {
+      const size_t idx = base + (size_t)k * line_stride;
+      V z = *reinterpret_cast<const V*>(zeta + idx);
+      const V dp = *reinterpret_cast<const V*>(dspec + idx);
+      z.x += alpha_prev * dp.x;
+      z.y += alpha_prev * dp.y;
+      *reinterpret_cast<V*>(zeta + idx) = z;
+      const T zz[2] = {z.x, z.y};
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T mu = (c ? mxb : mxa) + ml;
+        T rt = T(0), dd = T(0);
+        if (mu > T(0)) {
+          rt = h[c] - zz[c] / mu;
+          const T L = sl + s * mu + se2 * mu * mu + T(1) / mu;
+          dd = rt / L;
+          acc[3] += dd * dd / mu;
+        }
+        dv[c] = dd;
+        acc[0] += rt * dd;
+        acc[1] += dd * dd;
+        acc[2] += (mu * dd) * (mu * dd);
+        acc[4] += rt * rt;
+      }
+      V o;
+      o.x = dv[0];
+      o.y = dv[1];
+      *reinterpret_cast<V*>(dspec + idx) = o;
+    }
+    vr[q] = dv[0];
+    vi[q] = dv[1];
+  }
+  __syncthreads();  // every thread has read the forward spectrum
+  F::run(vr, vi, j, sr, si, twc, tws);
+  const T scale = (T)kp.inv_ntot;
+#pragma unroll
+  for (int q = 0; q < F::R; ++q) {
+    const int k = j + q * F::TS;
+    T h1, h2;
+    dht_split(sr, si, k, N, h1, h2);
+    V o;
+    o.x = h1 * scale;
+    o.y = h2 * scale;
+    *reinterpret_cast<V*>(data + base + (size_t)k * line_stride) = o;
+  }
+
+  double v[5];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) v[m] = (double)acc[m];
+  block_reduce<5, false>(v, sred);
+  if (publish_and_check_last(v, 5, partials, &ctrl->counter[CS_MID], &sflag)) {
+    double tot[5];
+    gather_partials<5, false>(tot, partials, sred);
+    if (tid == 0) {
+      const double w = kp.hd * kp.inv_ntot;
+      ctrl->rd = tot[0] * w;
+      ctrl->dd = tot[1] * w;
+      ctrl->lapdd = tot[2] * w;
+      ctrl->tdd = tot[3] * w;
+      if (ctrl->pre_eta > 0.0) {
+        const double pn = sqrt(fmax(ctrl->rd, 0.0));
+        if (ctrl->pre_ref <= 0.0) {
+          ctrl->pre_ref = pn;
+        } else if (pn < ctrl->pre_eta * ctrl->pre_ref) {
+          ctrl->status = 0;
+          ctrl->done = 1;
+        }
+      }
+      if (ORDER == 6) {
+        const double res = sqrt(tot[4] * w);
+        ctrl->res_l2 = res;
+        ctrl->res_linf = -1.0;
+        const int it = ctrl->iter;
+        if (ctrl->hist_res != nullptr && it < ctrl->hist_cap) ctrl->hist_res[it] = res;
+        if (!isfinite(res)) {
+          ctrl->status = 7;
+          ctrl->done = 1;
+        } else if (res < ctrl->tol) {
+          ctrl->status = 0;
+          ctrl->done = 1;
+        } else if (it >= ctrl->max_iter) {
+          ctrl->status = 4;
+          ctrl->done = 1;
+        }
+      }
+      // reset the line-search state for this iteration (general-p Newton:
+      // bracket [c1, c2] with c2 < 0 meaning "no upper end yet", c3 = done)
+      ctrl->c1 = 0.0;
+      ctrl->c2 = -1.0;
+      ctrl->c3 = 0.0;
+      ctrl->alpha = 0.0;
+      ctrl->counter[CS_MID] = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------ spectral helpers
+template <typename T>
+__device__ __forceinline__ T mu_at(size_t i, const KParams& kp, const T* sx, const T* sy, const T* sz) {
+  const int x = (int)(i % kp.nx);
+  const size_t rest = i / kp.nx;
+  const int y = (int)(rest % kp.ny);
+  const int z = (int)(rest / kp.ny);
+  return sx[x] + sy[y] + (kp.dim == 3 ? sz[z] : T(0));
+}
+
+template <typename T>
+__global__ void k_spec6_combine(T* a, const T* b, KParams kp, const T* sx, const T* sy, const T* sz, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T mu = mu_at(i, kp, sx, sy, sz);
+    a[i] = (mu > T(0)) ? a[i] - b[i] / mu : T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_spec_apply_T(T* a, KParams kp, const T* sx, const T* sy, const T* sz, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T mu = mu_at(i, kp, sx, sy, sz);
+    a[i] = (mu > T(0)) ? a[i] / mu : T(0);
+  }
+}
+
+// ------------------------------------------------------------ launch helpers
+template <typename T, int N>
+size_t pair_smem() {
+  return 2 * (size_t)(N + PAD) * sizeof(T);
+}
+
+// Number of column pairs per block: fill 256 threads, bounded by the shared
+// memory budget and by the available pairs; a power of two.
+template <typename T, int N>
+int pick_pairs(int avail_pairs) {
+  using F = LineFFT<T, N>;
+  int pairs = kThreads / F::TS;
+  while (pairs > 1 && (size_t)pairs * pair_smem<T, N>() > kMaxSmem) pairs >>= 1;
+  while (pairs > 1 && pairs > avail_pairs) pairs >>= 1;
+  return pairs < 1 ? 1 : pairs;
+}
+
+template <typename T, int N>
+cudaError_t rows_impl(const T* src, T* dst, int nrows, T scale, const int* done, const T* twc,
+                      const T* tws, cudaStream_t st) {
+  using F = LineFFT<T, N>;
+  const int pairs = pick_pairs<T, N>(1 << 30);
+  const int rows_per_block = 2 * pairs;
+  const int grid = (nrows + rows_per_block - 1) / rows_per_block;
+  k_dht_rows<T, N><<<grid, pairs * F::TS, pairs * pair_smem<T, N>(), st>>>(src, dst, nrows, scale, done,
+                                                                           twc, tws);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t cols_impl(T* data, int nx, int nouter, size_t line_stride, size_t outer_stride, T scale,
+                      const int* done, const T* twc, const T* tws, cudaStream_t st) {
+  using F = LineFFT<T, N>;
+  const int pairs = pick_pairs<T, N>(nx / 2);
+  dim3 grid(nx / (2 * pairs), nouter);
+  k_dht_cols<T, N><<<grid, pairs * F::TS, pairs * pair_smem<T, N>(), st>>>(data, line_stride, outer_stride,
+                                                                           scale, done, twc, tws);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t mid_impl(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* zeta, T* dspec,
+                     const AxisTables<T>& tb, cudaStream_t st) {
+  using F = LineFFT<T, N>;
+  const int nx = kp.nx;
+  const int pairs = pick_pairs<T, N>(nx / 2);
+  size_t line_stride, outer_stride;
+  int nouter;
+  const T* symo;
+  const T* syml;
+  const T* twc;
+  const T* tws;
+  if (kp.dim == 2) {
+    line_stride = nx;
+    outer_stride = 0;
+    nouter = 1;
+    symo = nullptr;
+    syml = tb.sym[1];
+    twc = tb.twc[1];
+    tws = tb.tws[1];
+  } else {
+    line_stride = (size_t)nx * kp.ny;
+    outer_stride = nx;
+    nouter = kp.ny;
+    symo = tb.sym[1];
+    syml = tb.sym[2];
+    twc = tb.twc[2];
+    tws = tb.tws[2];
+  }
+  dim3 grid(nx / (2 * pairs), nouter);
+  const size_t sm = pairs * pair_smem<T, N>();
+  if (kp.order == 4)
+    k_mid<T, N, 4><<<grid, pairs * F::TS, sm, st>>>(data, line_stride, outer_stride, kp, ctrl, partials,
+                                                   zeta, dspec, tb.sym[0], symo, syml, twc, tws);
+  else
+    k_mid<T, N, 6><<<grid, pairs * F::TS, sm, st>>>(data, line_stride, outer_stride, kp, ctrl, partials,
+                                                   zeta, dspec, tb.sym[0], symo, syml, twc, tws);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+void set_attrs() {
+  cudaFuncSetAttribute(k_dht_rows<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_cols<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_mid<T, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_mid<T, N, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+}
+
+#define PSD_DISPATCH_N(n, CALL)      \
+  switch (n) {                       \
+    case 8: { constexpr int NN = 8; return CALL; }       \
+    case 16: { constexpr int NN = 16; return CALL; }     \
+    case 32: { constexpr int NN = 32; return CALL; }     \
+    case 64: { constexpr int NN = 64; return CALL; }     \
+    case 128: { constexpr int NN = 128; return CALL; }   \
+    case 256: { constexpr int NN = 256; return CALL; }   \
+    case 512: { constexpr int NN = 512; return CALL; }   \
+    case 1024: { constexpr int NN = 1024; return CALL; } \
+    default: return cudaErrorInvalidValue;               \
+  }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_dht_rows(const T* src, T* dst, int nx, int nrows, T scale, const int* done,
+                            const AxisTables<T>& tb, cudaStream_t st) {
+  PSD_DISPATCH_N(nx, (rows_impl<T, NN>(src, dst, nrows, scale, done, tb.twc[0], tb.tws[0], st)));
+}
+
+template <typename T>
+cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const int* done,
+                            const AxisTables<T>& tb, cudaStream_t st) {
+  const int n = ax == 1 ? kp.ny : kp.nz;
+  size_t line_stride, outer_stride;
+  int nouter;
+  if (ax == 1) {
+    line_stride = kp.nx;
+    outer_stride = (size_t)kp.nx * kp.ny;
+    nouter = kp.nz;
+  } else {
+    line_stride = (size_t)kp.nx * kp.ny;
+    outer_stride = kp.nx;
+    nouter = kp.ny;
+  }
+  PSD_DISPATCH_N(n, (cols_impl<T, NN>(data, kp.nx, nouter, line_stride, outer_stride, scale, done,
+                                      tb.twc[ax], tb.tws[ax], st)));
+}
+
+template <typename T>
+cudaError_t launch_mid(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* zeta, T* dspec,
+                       const AxisTables<T>& tb, cudaStream_t st) {
+  const int n = kp.dim == 2 ? kp.ny : kp.nz;
+  PSD_DISPATCH_N(n, (mid_impl<T, NN>(data, kp, ctrl, partials, zeta, dspec, tb, st)));
+}
+
+template <typename T>
+cudaError_t launch_spec6_combine(T* a, const T* b, const KParams& kp, const AxisTables<T>& tb,
+                                 cudaStream_t st) {
+  const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+  k_spec6_combine<T><<<grid, 256, 0, st>>>(a, b, kp, tb.sym[0], tb.sym[1], tb.sym[2], n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_apply_T(T* a, const KParams& kp, const AxisTables<T>& tb, cudaStream_t st) {
+  const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+  k_spec_apply_T<T><<<grid, 256, 0, st>>>(a, kp, tb.sym[0], tb.sym[1], tb.sym[2], n);
+  return cudaGetLastError();
+}
+
+void init_dht_attributes() {
+  set_attrs<float, 8>();
+  set_attrs<float, 16>();
+  set_attrs<float, 32>();
+  set_attrs<float, 64>();
+  set_attrs<float, 128>();
+  set_attrs<float, 256>();
+  set_attrs<float, 512>();
+  set_attrs<float, 1024>();
+  set_attrs<double, 8>();
+  set_attrs<double, 16>();
+  set_attrs<double, 32>();
+  set_attrs<double, 64>();
+  set_attrs<double, 128>();
+  set_attrs<double, 256>();
+  set_attrs<double, 512>();
+  set_attrs<double, 1024>();
+}
+
+#define PSD_INST(T)                                                                                    \
+  template cudaError_t launch_dht_rows<T>(const T*, T*, int, int, T, const int*, const AxisTables<T>&, \
+                                          cudaStream_t);                                               \
+  template cudaError_t launch_dht_cols<T>(T*, const KParams&, int, T, const int*, const AxisTables<T>&, \
+                                          cudaStream_t);                                               \
+  template cudaError_t launch_mid<T>(T*, const KParams&, Ctrl*, double*, T*, T*, const AxisTables<T>&,  \
+                                     cudaStream_t);                                                    \
+  template cudaError_t launch_spec6_combine<T>(T*, const T*, const KParams&, const AxisTables<T>&,      \
+                                               cudaStream_t);                                          \
+  template cudaError_t launch_spec_apply_T<T>(T*, const KParams&, const AxisTables<T>&, cudaStream_t);
+PSD_INST(float)
+PSD_INST(double)
+
+}  // namespace psd

@@ -1,0 +1,90 @@
+// Internal launchers of the PSD CUDA kernels (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "psd_common.cuh"
+
+namespace psd {
+
+// Per-axis tables owned by a context, in both precisions.
+template <typename T>
+struct AxisTables {
+  const T* twc[3];  // cos(2 pi t / n_a), t < n_a
+  const T* tws[3];  // sin(2 pi t / n_a)
+  const T* sym[3];  // (4/h^2) sin^2(pi k / n_a), k < n_a
+};
+
+// ----------------------------------------------------------------- DHT passes
+// 1D DHT of every line along x (contiguous rows), src -> dst (may alias),
+// multiplied by `scale`.  Skipped when *done != 0 (done may be null).
+template <typename T>
+cudaError_t launch_dht_rows(const T* src, T* dst, int nx, int nrows, T scale, const int* done,
+                            const AxisTables<T>& tb, cudaStream_t st);
+
+// 1D DHT of every line along axis `ax` (1 = y, 2 = z), in place.
+template <typename T>
+cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const int* done,
+                            const AxisTables<T>& tb, cudaStream_t st);
+
+// The middle pass along the slowest axis (y in 2D, z in 3D) of the
+// preconditioner: forward DHT, division by the symbol of L_h, Parseval sums
+// into ctrl, inverse DHT (with the 1/N of the whole transform).  Order 6 also
+// advances zeta += alpha * dspec, subtracts zeta/mu (the T_h[u - g] term),
+// stores the new direction spectrum in dspec and decides convergence on the
+// spectral residual norm.
+template <typename T>
+cudaError_t launch_mid(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* zeta, T* dspec,
+                       const AxisTables<T>& tb, cudaStream_t st);
+
+// Spectral helpers (order 6, off the hot loop).
+// spec6_combine: a <- (mu == 0) ? 0 : a - b / mu   (a, b full DHT spectra)
+// spec_apply_T:  a <- (mu == 0) ? 0 : a / mu
+template <typename T>
+cudaError_t launch_spec6_combine(T* a, const T* b, const KParams& kp, const AxisTables<T>& tb,
+                                 cudaStream_t st);
+template <typename T>
+cudaError_t launch_spec_apply_T(T* a, const KParams& kp, const AxisTables<T>& tb, cudaStream_t st);
+
+// ------------------------------------------------------------------ stencils
+enum ResMode { RM_PLAIN = 0, RM_INNER = 1 };
+
+template <typename T>
+struct ResArgs {
+  const T* u_in;   // plain: iterate u; inner: correction delta
+  const T* d;      // direction applied before evaluation (null: none)
+  T* u_out;        // receives u_in + alpha d (only when d != null)
+  const T* f;      // plain: right-hand side f; inner: outer residual R
+  const T* ubase;  // inner: the outer iterate (rounded); else null
+  T* r;            // residual (order 6: local part, without T_h)
+  int norm;        // 1: reduce ||r|| into ctrl and decide convergence
+  int update_iter; // 1: this call advances the iteration count
+};
+
+// r = f - N_h^{loc}[u_in + alpha d] (plain) or
+// r = R - (N_h^{loc}[ubase + delta] - N_h^{loc}[ubase]) (inner, in a
+// cancellation-free form), N_h^{loc} = cu I - s plap + s eps^2 Delta_h^2.
+template <typename T>
+cudaError_t launch_residual(const ResArgs<T>& a, int mode, int pk, const KParams& kp, Ctrl* ctrl,
+                            double* partials, cudaStream_t st);
+
+// Line search reduction over the vertices: a = grad(u [+ ubase]), b = grad(d).
+// p = 4: the cubic coefficients, then the step size alpha by safeguarded
+// Newton in the last block.  General p: one Newton step per launch.
+template <typename T>
+cudaError_t launch_linesearch(const T* u, const T* ubase, const T* d, int pk, const KParams& kp,
+                              Ctrl* ctrl, double* partials, cudaStream_t st);
+
+// ------------------------------------------------------------------ misc
+// y = a * x + b * z + c elementwise (x or z may be null = 0; may alias y).
+template <typename T>
+cudaError_t launch_axpby(T* y, const T* x, const T* z, double a, double b, double c, size_t n, cudaStream_t st);
+// sum x -> c->rd, sqrt(hd sum x^2) -> c->res_l2, max|x| -> c->res_linf.
+cudaError_t launch_norms(const double* x, size_t n, double hd, Ctrl* c, double* partials, cudaStream_t st);
+// out = (float) in;  u += delta, u32 = (float) u  (mixed precision bookkeeping)
+cudaError_t launch_round_f32(float* out, const double* in, size_t n, cudaStream_t st);
+cudaError_t launch_accumulate_f64(double* u, const float* delta, float* u32, size_t n, cudaStream_t st);
+
+void init_dht_attributes();
+
+}  // namespace psd

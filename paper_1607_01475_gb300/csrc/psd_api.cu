@@ -1,0 +1,769 @@
+// C ABI of the PSD library (include/psd.h): context management, the PSD
+// driver loops (plain FP64 and mixed FP32/FP64 with outer FP64 residual
+// correction), and the stand-alone residual / preconditioner calls.
+//
+// One PSD iteration (Algorithm 1 structure, Sec. 2.2, Sec. 6.1) is a fixed
+// sequence of launches on the handle's stream:
+//   DHT x -> [DHT y] -> middle pass (last axis: DHT, divide by the symbol of
+//   L_h, Parseval sums, inverse DHT) -> [DHT y] -> DHT x (= d)
+//   -> line search (alpha) -> residual at u + alpha d (fused update).
+// The step size, the iteration count and the stop flag live in device memory
+// (Ctrl); every kernel returns at once when the stop flag is set, so the host
+// enqueues chunks of iterations and reads the flag once per chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/psd.h"
+#include "kernels.h"
+
+using psd::AxisTables;
+using psd::Ctrl;
+using psd::KParams;
+using psd::ResArgs;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kChunk = 8;          // iterations enqueued between host checks
+constexpr int kLsPassesGen = 16;   // Newton passes of the general-p line search
+constexpr double kInnerEta = 1e-5;  // inner FP32 solve: relative drop of the preconditioned norm
+constexpr int kInnerMaxIter = 400;  // inner FP32 iterations per outer correction
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+struct psd_context {
+  psd_params prm{};
+  KParams kp{};
+  int pk = psd::PK_GEN;
+  cudaStream_t st = nullptr;
+  size_t N = 0;
+  std::string err;
+
+  void* tables = nullptr;
+  AxisTables<double> tb64{};
+  AxisTables<float> tb32{};
+
+  // FP64 work arrays
+  double* ub = nullptr;     // second iterate buffer (ping-pong with the caller's u)
+  double* W = nullptr;      // residual / transform work array
+  double* D = nullptr;      // search direction
+  double* Z = nullptr;      // order 6: DHT spectrum of u - g
+  double* Dsp = nullptr;    // order 6: DHT spectrum of the direction
+  // FP32 work arrays (mixed)
+  float* u32 = nullptr;
+  float* da = nullptr;
+  float* db = nullptr;
+  float* W32 = nullptr;
+  float* D32 = nullptr;
+  float* R32 = nullptr;
+  float* Z32 = nullptr;
+  float* Dsp32 = nullptr;
+
+  double* partials = nullptr;
+  Ctrl* ctrl = nullptr;   // PSD run state
+  Ctrl* ctrl2 = nullptr;  // auxiliary reductions (outer residual, norms)
+  Ctrl* h_ctrl = nullptr; // pinned host mirror
+
+  double* d_hist = nullptr;
+  double* user_alpha = nullptr;
+  double* user_res = nullptr;
+  int hist_cap = 0;
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // tracing: event pairs around every launch while enabled
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec {
+    int cls;
+    int a, b;
+  };
+  std::vector<Rec> recs;
+  double prof_ms[PSD_PROF_CLASSES] = {};
+  long long prof_n[PSD_PROF_CLASSES] = {};
+  std::vector<float> prof_durs[PSD_PROF_CLASSES];  // per-launch durations (ms)
+};
+
+namespace {
+
+psd_status fail(psd_context* c, psd_status s, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(c, PSD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+
+template <typename T>
+psd_status alloc(psd_context* c, T** p, size_t n) {
+  if (*p) return PSD_OK;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, PSD_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return PSD_OK;
+}
+
+#define TRY(x)                   \
+  do {                           \
+    psd_status s_ = (x);         \
+    if (s_ != PSD_OK) return s_; \
+  } while (0)
+
+psd_status validate(const psd_params* p, std::string& why) {
+  if (!p) return why = "params is NULL", PSD_ERR_INVALID;
+  if (p->order != 4 && p->order != 6) return why = "order must be 4 or 6", PSD_ERR_INVALID;
+  if (p->dim != 2 && p->dim != 3) return why = "dim must be 2 or 3", PSD_ERR_INVALID;
+  for (int a = 0; a < p->dim; ++a)
+    if (!is_pow2(p->n[a]) || p->n[a] < 8 || p->n[a] > 1024)
+      return why = "n[a] must be a power of two in [8, 1024]", PSD_ERR_INVALID;
+  if (p->dim == 2 && p->n[2] != 1) return why = "n[2] must be 1 in 2D", PSD_ERR_INVALID;
+  if (!(p->h > 0) || !std::isfinite(p->h)) return why = "h must be positive", PSD_ERR_INVALID;
+  if (!(p->p >= 2) || !std::isfinite(p->p)) return why = "p must be >= 2", PSD_ERR_INVALID;
+  if (p->dim == 3 && p->p > 6) return why = "3D requires p <= 6", PSD_ERR_INVALID;
+  if (!(p->s > 0) || !std::isfinite(p->s)) return why = "s must be positive", PSD_ERR_INVALID;
+  if (!(p->eps > 0) || !std::isfinite(p->eps)) return why = "eps must be positive", PSD_ERR_INVALID;
+  if (!(p->lambda >= 0) || !std::isfinite(p->lambda)) return why = "lambda must be >= 0", PSD_ERR_INVALID;
+  if (p->precision != PSD_FP64 && p->precision != PSD_MIXED)
+    return why = "precision must be PSD_FP64 or PSD_MIXED", PSD_ERR_INVALID;
+  if (!(p->tol >= 0) || !std::isfinite(p->tol)) return why = "tol must be >= 0", PSD_ERR_INVALID;
+  if (p->max_iter < 0) return why = "max_iter must be >= 0", PSD_ERR_INVALID;
+  if (p->precision == PSD_MIXED && p->max_outer < 1) return why = "max_outer must be >= 1", PSD_ERR_INVALID;
+  return PSD_OK;
+}
+
+psd_status build_tables(psd_context* c) {
+  const int dim = c->prm.dim;
+  int n[3] = {c->prm.n[0], c->prm.n[1], dim == 3 ? c->prm.n[2] : 1};
+  size_t tot = 0;
+  for (int a = 0; a < 3; ++a) tot += 3 * (size_t)n[a];
+  std::vector<double> h64(tot);
+  std::vector<float> h32(tot);
+  size_t off = 0;
+  size_t offs[3][3];
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double h = c->prm.h;
+  for (int a = 0; a < 3; ++a) {
+    offs[a][0] = off;
+    for (int t = 0; t < n[a]; ++t) h64[off + t] = (double)cosl(2.0L * pi * t / n[a]);
+    off += n[a];
+    offs[a][1] = off;
+    for (int t = 0; t < n[a]; ++t) h64[off + t] = (double)sinl(2.0L * pi * t / n[a]);
+    off += n[a];
+    offs[a][2] = off;
+    for (int k = 0; k < n[a]; ++k) {
+      const long double sn = (n[a] > 1) ? sinl(pi * k / n[a]) : 0.0L;
+      h64[off + k] = (double)(4.0L / (h * h) * sn * sn);
+    }
+    off += n[a];
+  }
+  for (size_t i = 0; i < tot; ++i) h32[i] = (float)h64[i];
+  CK(cudaMalloc(&c->tables, tot * (sizeof(double) + sizeof(float))));
+  double* d64 = (double*)c->tables;
+  float* d32 = (float*)(d64 + tot);
+  CK(cudaMemcpy(d64, h64.data(), tot * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d32, h32.data(), tot * sizeof(float), cudaMemcpyHostToDevice));
+  for (int a = 0; a < 3; ++a) {
+    c->tb64.twc[a] = d64 + offs[a][0];
+    c->tb64.tws[a] = d64 + offs[a][1];
+    c->tb64.sym[a] = d64 + offs[a][2];
+    c->tb32.twc[a] = d32 + offs[a][0];
+    c->tb32.tws[a] = d32 + offs[a][1];
+    c->tb32.sym[a] = d32 + offs[a][2];
+  }
+  return PSD_OK;
+}
+
+// ---------------------------------------------------------------- tracing
+// Fold finished event pairs into the per-class totals and recycle the pool.
+psd_status prof_flush(psd_context* c) {
+  if (c->recs.empty()) return PSD_OK;
+  CK(cudaStreamSynchronize(c->st));
+  for (const auto& r : c->recs) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev_pool[r.a], c->ev_pool[r.b]));
+    c->prof_ms[r.cls] += ms;
+    c->prof_n[r.cls] += 1;
+    c->prof_durs[r.cls].push_back(ms);
+  }
+  c->recs.clear();
+  return PSD_OK;
+}
+
+// RAII bracket of one launch: records a start event now and a stop event at
+// scope exit (both on the handle's stream).
+struct ProfScope {
+  psd_context* c;
+  int cls;
+  int a = -1;
+  ProfScope(psd_context* c_, int cls_) : c(c_), cls(cls_) {
+    if (!c->prof) return;
+    const size_t need = 2 * (c->recs.size() + 1);
+    if (need > c->ev_pool.size()) {
+      if (c->ev_pool.size() >= 4096) {
+        if (prof_flush(c) != PSD_OK) return;
+      } else {
+        const size_t grow = std::max<size_t>(256, c->ev_pool.size());
+        for (size_t i = 0; i < grow; ++i) {
+          cudaEvent_t e;
+          if (cudaEventCreate(&e) != cudaSuccess) return;
+          c->ev_pool.push_back(e);
+        }
+      }
+    }
+    a = (int)(2 * c->recs.size());
+    if (cudaEventRecord(c->ev_pool[a], c->st) != cudaSuccess) a = -1;
+  }
+  ~ProfScope() {
+    if (a < 0) return;
+    if (cudaEventRecord(c->ev_pool[a + 1], c->st) == cudaSuccess) c->recs.push_back({cls, a, a + 1});
+  }
+};
+
+template <typename T>
+constexpr int cls_of(int fp64cls) {
+  return sizeof(T) == 8 ? fp64cls : fp64cls + 1;
+}
+
+void init_ctrl(Ctrl& h, double tol, int max_iter) {
+  std::memset(&h, 0, sizeof(h));
+  h.tol = tol;
+  h.max_iter = max_iter;
+  h.res_linf = -1.0;
+  h.c2 = -1.0;
+}
+
+psd_status upload_ctrl(psd_context* c, Ctrl* dst, const Ctrl& h) {
+  *c->h_ctrl = h;
+  CK(cudaMemcpyAsync(dst, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return PSD_OK;
+}
+
+psd_status read_ctrl(psd_context* c, const Ctrl* src, Ctrl& out) {
+  CK(cudaMemcpyAsync(c->h_ctrl, src, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  out = *c->h_ctrl;
+  return PSD_OK;
+}
+
+// Full separable DHT of x in place, multiplied by `scale` (its own inverse
+// when scale = 1/N).
+template <typename T>
+psd_status full_dht(psd_context* c, T* x, T scale, const AxisTables<T>& tb) {
+  const KParams& kp = c->kp;
+  const int nrows = kp.ny * kp.nz;
+  if (kp.dim == 2) {
+    { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_ROWS_FP64)); CK(psd::launch_dht_rows<T>(x, x, kp.nx, nrows, T(1), nullptr, tb, c->st)); }
+    { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_COLS_FP64)); CK(psd::launch_dht_cols<T>(x, kp, 1, scale, nullptr, tb, c->st)); }
+  } else {
+    { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_ROWS_FP64)); CK(psd::launch_dht_rows<T>(x, x, kp.nx, nrows, T(1), nullptr, tb, c->st)); }
+    { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_COLS_FP64)); CK(psd::launch_dht_cols<T>(x, kp, 1, T(1), nullptr, tb, c->st)); }
+    { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_COLS_FP64)); CK(psd::launch_dht_cols<T>(x, kp, 2, scale, nullptr, tb, c->st)); }
+  }
+  return PSD_OK;
+}
+
+// The search-direction solve L_h d = W of one PSD iteration (W is consumed).
+template <typename T>
+psd_status precond_passes(psd_context* c, T* W, T* D, Ctrl* ctrl, T* zeta, T* dspec, const AxisTables<T>& tb) {
+  const KParams& kp = c->kp;
+  const int* done = &ctrl->done;
+  const int nrows = kp.ny * kp.nz;
+  { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_ROWS_FP64)); CK(psd::launch_dht_rows<T>(W, W, kp.nx, nrows, T(1), done, tb, c->st)); }
+  if (kp.dim == 3) { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_COLS_FP64)); CK(psd::launch_dht_cols<T>(W, kp, 1, T(1), done, tb, c->st)); }
+  { ProfScope p_(c, cls_of<T>(PSD_PROF_MID_FP64)); CK(psd::launch_mid<T>(W, kp, ctrl, c->partials, zeta, dspec, tb, c->st)); }
+  if (kp.dim == 3) { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_COLS_FP64)); CK(psd::launch_dht_cols<T>(W, kp, 1, T(1), done, tb, c->st)); }
+  { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_ROWS_FP64)); CK(psd::launch_dht_rows<T>(W, D, kp.nx, nrows, T(1), done, tb, c->st)); }
+  return PSD_OK;
+}
+
+template <typename T>
+psd_status linesearch(psd_context* c, const T* u, const T* ubase, const T* D, Ctrl* ctrl) {
+  const int passes = (c->pk == psd::PK_4) ? 1 : kLsPassesGen;
+  for (int i = 0; i < passes; ++i) {
+    ProfScope p_(c, cls_of<T>(PSD_PROF_LINESEARCH_FP64));
+    CK(psd::launch_linesearch<T>(u, ubase, D, c->pk, c->kp, ctrl, c->partials, c->st));
+  }
+  return PSD_OK;
+}
+
+psd_status ensure_fp64(psd_context* c) {
+  TRY(alloc(c, &c->ub, c->N));
+  TRY(alloc(c, &c->W, c->N));
+  TRY(alloc(c, &c->D, c->N));
+  if (c->prm.order == 6) {
+    TRY(alloc(c, &c->Z, c->N));
+    TRY(alloc(c, &c->Dsp, c->N));
+  }
+  return PSD_OK;
+}
+
+psd_status ensure_fp32(psd_context* c) {
+  TRY(alloc(c, &c->u32, c->N));
+  TRY(alloc(c, &c->da, c->N));
+  TRY(alloc(c, &c->db, c->N));
+  TRY(alloc(c, &c->W32, c->N));
+  TRY(alloc(c, &c->D32, c->N));
+  TRY(alloc(c, &c->R32, c->N));
+  if (c->prm.order == 6) {
+    TRY(alloc(c, &c->Z32, c->N));
+    TRY(alloc(c, &c->Dsp32, c->N));
+  }
+  return PSD_OK;
+}
+
+// FP64 residual r = f - N_h[u] into r (order 6: P0[...] including T_h[u - g]),
+// norms into ctrl2 (res_l2, res_linf).  Uses W, Z as scratch (order 6).
+psd_status residual64(psd_context* c, const double* u, const double* f, const double* g, double* r) {
+  const KParams& kp = c->kp;
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, r, kp.order == 4 ? 1 : 0, 0};
+  { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
+  if (kp.order == 6) {
+    // r <- P0[r_loc - T_h[u - g]] through the spectrum
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
+    TRY(full_dht<double>(c, c->Z, 1.0, c->tb64));
+    TRY(full_dht<double>(c, r, 1.0, c->tb64));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec6_combine<double>(r, c->Z, kp, c->tb64, c->st)); }
+    TRY(full_dht<double>(c, r, kp.inv_ntot, c->tb64));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(r, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+  }
+  return PSD_OK;
+}
+
+// Plain FP64 PSD.
+psd_status solve_fp64(psd_context* c, const double* f, const double* g, double* u, psd_info* info) {
+  TRY(ensure_fp64(c));
+  const KParams& kp = c->kp;
+  Ctrl h;
+  init_ctrl(h, c->prm.tol, c->prm.max_iter);
+  if (c->hist_cap > 0) {
+    h.hist_cap = c->hist_cap;
+    h.hist_alpha = c->d_hist;
+    h.hist_res = c->d_hist + c->hist_cap;
+  }
+  TRY(upload_ctrl(c, c->ctrl, h));
+  CK(cudaEventRecord(c->ev0, c->st));
+  if (kp.order == 6) {
+    CK(cudaMemsetAsync(c->Dsp, 0, c->N * sizeof(double), c->st));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
+    TRY(full_dht<double>(c, c->Z, 1.0, c->tb64));
+  }
+  {
+    ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, kp.order == 4 ? 1 : 0, 0};
+    { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl, c->partials, c->st)); }
+  }
+  int k = 0;
+  Ctrl hc;
+  for (;;) {
+    for (int i = 0; i < kChunk; ++i, ++k) {
+      double* cur = (k % 2 == 0) ? u : c->ub;
+      double* nxt = (k % 2 == 0) ? c->ub : u;
+      TRY(precond_passes<double>(c, c->W, c->D, c->ctrl, c->Z, c->Dsp, c->tb64));
+      TRY(linesearch<double>(c, cur, nullptr, c->D, c->ctrl));
+      ResArgs<double> a{cur, c->D, nxt, f, nullptr, c->W, kp.order == 4 ? 1 : 0, 1};
+      { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl, c->partials, c->st)); }
+    }
+    TRY(read_ctrl(c, c->ctrl, hc));
+    if (hc.done) break;
+    if (k > c->prm.max_iter + 2 * kChunk) {  // host-side guard: never loop unbounded
+      hc.status = PSD_ERR_NOCONV;
+      break;
+    }
+  }
+  CK(cudaEventRecord(c->ev1, c->st));
+  if (hc.iter % 2 == 1) CK(cudaMemcpyAsync(u, c->ub, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  if (info) {
+    info->iters = hc.iter;
+    info->outer_iters = 0;
+    info->res_l2 = hc.res_l2;
+    info->res_linf = hc.res_linf;
+    info->last_alpha = hc.alpha;
+    info->wall_ms = ms;
+    info->status = hc.status;
+  }
+  return (psd_status)hc.status;
+}
+
+// Mixed precision: outer FP64 residual R = f - N_h[u] (order 6: P0[...]
+// with the exact T_h[u - g]); inner FP32 PSD on the correction delta with
+// residual R - (N_h[u + delta] - N_h[u]) (order 6: mean-projected, the T_h
+// term kept as the DHT spectrum of delta); u += delta in FP64.
+psd_status solve_mixed(psd_context* c, const double* f, const double* g, double* u, psd_info* info) {
+  TRY(ensure_fp64(c));
+  TRY(ensure_fp32(c));
+  const KParams& kp = c->kp;
+  const bool six = kp.order == 6;
+  CK(cudaEventRecord(c->ev0, c->st));
+  double gbar = 0.0;
+  if (six) {
+    Ctrl hg;
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(g, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+    TRY(read_ctrl(c, c->ctrl2, hg));
+    gbar = hg.rd / (double)c->N;
+  }
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
+  int inner_total = 0, outer = 0;
+  int status = PSD_ERR_NOCONV;
+  double res = NAN, resinf = -1, last_alpha = 0;
+  const float* delta = nullptr;
+  for (;;) {
+    if (delta) {
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, delta, c->u32, c->N, c->st)); }
+      if (six) {
+        // keep mean(u) = mean(g) exactly: delta is mean-zero only up to FP32 rounding
+        Ctrl hu;
+        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+        TRY(read_ctrl(c, c->ctrl2, hu));
+        const double shift = gbar - hu.rd / (double)c->N;
+        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(u, u, nullptr, 1.0, 0.0, shift, c->N, c->st)); }
+        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
+      }
+    }
+    TRY(residual64(c, u, f, g, c->W));
+    ++outer;
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->R32, c->W, c->N, c->st)); }
+    Ctrl h2;
+    TRY(read_ctrl(c, c->ctrl2, h2));
+    res = h2.res_l2;
+    resinf = h2.res_linf;
+    if (!std::isfinite(res)) {
+      status = PSD_ERR_NONFINITE;
+      break;
+    }
+    if (res < c->prm.tol) {
+      status = PSD_OK;
+      break;
+    }
+    if (outer > c->prm.max_outer || inner_total >= c->prm.max_iter) {
+      status = PSD_ERR_NOCONV;
+      break;
+    }
+    // The FP32 residual of s eps^2 Delta_h^2 delta carries rounding noise of
+    // order eps32 * 64 s eps^2 / h^4 * |delta|, which on fine grids is as large
+    // as the residual itself, so ||r||_2 cannot serve as the inner stopping
+    // test.  The preconditioned norm (r, L_h^{-1} r)^{1/2} damps that noise by
+    // the symbol of L_h; the inner solve stops when it has dropped by kInnerEta.
+    Ctrl h;
+    init_ctrl(h, 0.0, std::min(c->prm.max_iter - inner_total, kInnerMaxIter));
+    h.pre_eta = kInnerEta;
+    TRY(upload_ctrl(c, c->ctrl, h));
+    CK(cudaMemsetAsync(c->da, 0, c->N * sizeof(float), c->st));
+    if (six) {
+      CK(cudaMemsetAsync(c->Z32, 0, c->N * sizeof(float), c->st));
+      CK(cudaMemsetAsync(c->Dsp32, 0, c->N * sizeof(float), c->st));
+    }
+    const int norm = six ? 0 : 1;
+    {
+      ResArgs<float> a{c->da, nullptr, nullptr, c->R32, c->u32, c->W32, norm, 0};
+      { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_INNER, c->pk, kp, c->ctrl, c->partials, c->st)); }
+    }
+    int k = 0;
+    Ctrl hc;
+    for (;;) {
+      for (int i = 0; i < kChunk; ++i, ++k) {
+        float* cur = (k % 2 == 0) ? c->da : c->db;
+        float* nxt = (k % 2 == 0) ? c->db : c->da;
+        TRY(precond_passes<float>(c, c->W32, c->D32, c->ctrl, c->Z32, c->Dsp32, c->tb32));
+        TRY(linesearch<float>(c, cur, c->u32, c->D32, c->ctrl));
+        ResArgs<float> a{cur, c->D32, nxt, c->R32, c->u32, c->W32, norm, 1};
+        { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_INNER, c->pk, kp, c->ctrl, c->partials, c->st)); }
+      }
+      TRY(read_ctrl(c, c->ctrl, hc));
+      if (hc.done) break;
+      if (k > h.max_iter + 2 * kChunk) break;  // host-side guard
+    }
+    inner_total += hc.iter;
+    last_alpha = hc.alpha;
+    if (hc.status == PSD_ERR_NONFINITE) {
+      status = PSD_ERR_NONFINITE;
+      break;
+    }
+    delta = (hc.iter % 2 == 0) ? c->da : c->db;
+    if (hc.iter == 0) delta = nullptr;
+  }
+  CK(cudaEventRecord(c->ev1, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  if (info) {
+    info->iters = inner_total;
+    info->outer_iters = outer;
+    info->res_l2 = res;
+    info->res_linf = resinf;
+    info->last_alpha = last_alpha;
+    info->wall_ms = ms;
+    info->status = status;
+  }
+  return (psd_status)status;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char* psd_status_string(psd_status s) {
+  switch (s) {
+    case PSD_OK: return "PSD_OK";
+    case PSD_ERR_INVALID: return "PSD_ERR_INVALID";
+    case PSD_ERR_NOMEM: return "PSD_ERR_NOMEM";
+    case PSD_ERR_CUDA: return "PSD_ERR_CUDA";
+    case PSD_ERR_NOCONV: return "PSD_ERR_NOCONV";
+    case PSD_ERR_TIMEOUT: return "PSD_ERR_TIMEOUT";
+    case PSD_ERR_UNSUPPORTED: return "PSD_ERR_UNSUPPORTED";
+    case PSD_ERR_NONFINITE: return "PSD_ERR_NONFINITE";
+  }
+  return "PSD_UNKNOWN_STATUS";
+}
+
+psd_status psd_create(const psd_params* params, psd_handle* out) {
+  psd_context* c = nullptr;
+  if (!out) return fail(nullptr, PSD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  psd_status s = validate(params, why);
+  if (s != PSD_OK) return fail(nullptr, s, why);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, PSD_ERR_CUDA, "no CUDA device");
+  }
+  c = new psd_context();
+  c->prm = *params;
+  c->st = (cudaStream_t)params->stream;
+  KParams& kp = c->kp;
+  kp.nx = params->n[0];
+  kp.ny = params->n[1];
+  kp.nz = params->dim == 3 ? params->n[2] : 1;
+  kp.dim = params->dim;
+  kp.h = params->h;
+  kp.inv_h = 1.0 / params->h;
+  kp.s = params->s;
+  kp.eps2 = params->eps * params->eps;
+  kp.lam = params->lambda;
+  kp.p = params->p;
+  kp.order = params->order;
+  kp.cu = params->order == 4 ? 1.0 : params->s * params->lambda;
+  kp.hd = params->dim == 3 ? params->h * params->h * params->h : params->h * params->h;
+  c->N = (size_t)kp.nx * kp.ny * kp.nz;
+  kp.inv_ntot = 1.0 / (double)c->N;
+  c->pk = (params->p == 4.0) ? psd::PK_4 : psd::PK_GEN;
+  static bool attrs = false;
+  if (!attrs) {
+    psd::init_dht_attributes();
+    attrs = true;
+  }
+  auto bail = [&](psd_status st) {
+    g_create_error = c->err;
+    psd_destroy(c);
+    return st;
+  };
+  if ((s = build_tables(c)) != PSD_OK) return bail(s);
+  const size_t npart = std::max<size_t>(c->N / 16, 4096) * 8;
+  if ((s = alloc(c, &c->partials, npart)) != PSD_OK) return bail(s);
+  if ((s = alloc(c, &c->ctrl, 1)) != PSD_OK) return bail(s);
+  if ((s = alloc(c, &c->ctrl2, 1)) != PSD_OK) return bail(s);
+  if (cudaMemset(c->ctrl, 0, sizeof(Ctrl)) != cudaSuccess || cudaMemset(c->ctrl2, 0, sizeof(Ctrl)) != cudaSuccess) {
+    c->err = "cudaMemset failed";
+    return bail(PSD_ERR_CUDA);
+  }
+  if (cudaMallocHost((void**)&c->h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+    cudaGetLastError();
+    c->err = "cudaMallocHost failed";
+    return bail(PSD_ERR_NOMEM);
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    c->err = "cudaEventCreate failed";
+    return bail(PSD_ERR_CUDA);
+  }
+  if ((s = ensure_fp64(c)) != PSD_OK) return bail(s);
+  if (params->precision == PSD_MIXED && (s = ensure_fp32(c)) != PSD_OK) return bail(s);
+  *out = c;
+  return PSD_OK;
+}
+
+psd_status psd_destroy(psd_handle c) {
+  if (!c) return PSD_OK;
+  void* ptrs[] = {c->tables, c->ub, c->W, c->D, c->Z, c->Dsp, c->u32, c->da, c->db, c->W32, c->D32,
+                  c->R32, c->Z32, c->Dsp32, c->partials, c->ctrl, c->ctrl2, c->d_hist};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+  return PSD_OK;
+}
+
+psd_status psd_profile(psd_handle c, int enable) {
+  if (!c) return PSD_ERR_INVALID;
+  if (enable) {
+    if (c->prof) TRY(prof_flush(c));
+    c->recs.clear();
+    for (int k = 0; k < PSD_PROF_CLASSES; ++k) {
+      c->prof_ms[k] = 0.0;
+      c->prof_n[k] = 0;
+      c->prof_durs[k].clear();
+    }
+  } else {
+    TRY(prof_flush(c));
+  }
+  c->prof = enable != 0;
+  return PSD_OK;
+}
+
+psd_status psd_profile_read(psd_handle c, double* ms, long long* launches, double* eff_ms, long long* eff_launches,
+                            double eff_us, int n) {
+  if (!c || n < 0 || n > PSD_PROF_CLASSES) return PSD_ERR_INVALID;
+  TRY(prof_flush(c));
+  for (int k = 0; k < n; ++k) {
+    if (ms) ms[k] = c->prof_ms[k];
+    if (launches) launches[k] = c->prof_n[k];
+    double em = 0.0;
+    long long en = 0;
+    for (float d : c->prof_durs[k])
+      if (d * 1000.0 > eff_us) {
+        em += d;
+        ++en;
+      }
+    if (eff_ms) eff_ms[k] = em;
+    if (eff_launches) eff_launches[k] = en;
+  }
+  return PSD_OK;
+}
+
+const char* psd_profile_class_name(int k) {
+  static const char* names[PSD_PROF_CLASSES] = {
+      "residual_fp64", "residual_fp32", "dht_rows_fp64", "dht_rows_fp32", "dht_cols_fp64", "dht_cols_fp32",
+      "mid_fp64",      "mid_fp32",      "linesearch_fp64", "linesearch_fp32", "other"};
+  return (k >= 0 && k < PSD_PROF_CLASSES) ? names[k] : nullptr;
+}
+
+psd_status psd_last_error(psd_handle c, char* buf, size_t len) {
+  if (!buf || len == 0) return PSD_ERR_INVALID;
+  const std::string& e = c ? c->err : g_create_error;
+  std::snprintf(buf, len, "%s", e.c_str());
+  return PSD_OK;
+}
+
+psd_status psd_set_history(psd_handle c, double* alpha_hist, double* res_hist, int cap) {
+  if (!c) return PSD_ERR_INVALID;
+  if (cap < 0) return fail(c, PSD_ERR_INVALID, "cap must be >= 0");
+  if (c->d_hist) {
+    cudaFree(c->d_hist);
+    c->d_hist = nullptr;
+  }
+  c->hist_cap = 0;
+  c->user_alpha = alpha_hist;
+  c->user_res = res_hist;
+  if ((alpha_hist || res_hist) && cap > 0) {
+    TRY(alloc(c, &c->d_hist, 2 * (size_t)cap));
+    c->hist_cap = cap;
+  }
+  return PSD_OK;
+}
+
+psd_status psd_residual(psd_handle c, const double* u, const double* f, const double* g, double* r,
+                        double* res_l2, double* res_linf) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u || !f) return fail(c, PSD_ERR_INVALID, "u and f are required");
+  if (c->prm.order == 6 && !g) return fail(c, PSD_ERR_INVALID, "order 6 requires g");
+  TRY(ensure_fp64(c));
+  double* out = r ? r : c->D;
+  TRY(residual64(c, u, f, g, out));
+  Ctrl h;
+  TRY(read_ctrl(c, c->ctrl2, h));
+  if (res_l2) *res_l2 = h.res_l2;
+  if (res_linf) *res_linf = h.res_linf;
+  return PSD_OK;
+}
+
+psd_status psd_residual_f32(psd_handle c, const float* u, const float* f, float* r) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u || !f || !r) return fail(c, PSD_ERR_INVALID, "u, f and r are required");
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  ResArgs<float> a{u, nullptr, nullptr, f, nullptr, r, 0, 0};
+  { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_PLAIN, c->pk, c->kp, c->ctrl2, c->partials, c->st)); }
+  CK(cudaStreamSynchronize(c->st));
+  return PSD_OK;
+}
+
+psd_status psd_precond_solve(psd_handle c, const double* r, double* d) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!r || !d) return fail(c, PSD_ERR_INVALID, "r and d are required");
+  TRY(ensure_fp64(c));
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  if (d != r) CK(cudaMemcpyAsync(d, r, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  if (c->prm.order == 6) {
+    CK(cudaMemsetAsync(c->Z, 0, c->N * sizeof(double), c->st));
+    CK(cudaMemsetAsync(c->Dsp, 0, c->N * sizeof(double), c->st));
+  }
+  TRY(precond_passes<double>(c, d, d, c->ctrl2, c->Z, c->Dsp, c->tb64));
+  return PSD_OK;
+}
+
+psd_status psd_solve(psd_handle c, const double* f, const double* g, double* u, double* w, psd_info* info) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!f || !u) return fail(c, PSD_ERR_INVALID, "f and u are required");
+  if (c->prm.order == 6 && !g) return fail(c, PSD_ERR_INVALID, "order 6 requires g");
+  psd_status s = (c->prm.precision == PSD_MIXED) ? solve_mixed(c, f, g, u, info) : solve_fp64(c, f, g, u, info);
+  if (s == PSD_ERR_CUDA || s == PSD_ERR_NOMEM || s == PSD_ERR_UNSUPPORTED) return s;
+  if (c->hist_cap > 0 && c->prm.precision == PSD_FP64) {
+    if (c->user_alpha)
+      CK(cudaMemcpy(c->user_alpha, c->d_hist, c->hist_cap * sizeof(double), cudaMemcpyDeviceToHost));
+    if (c->user_res)
+      CK(cudaMemcpy(c->user_res, c->d_hist + c->hist_cap, c->hist_cap * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  if (c->prm.order == 6 && w) {
+    // w = -T_h[u - g] + s lambda mean(g) - mean(f)
+    const KParams& kp = c->kp;
+    Ctrl hg, hf;
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(g, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+    TRY(read_ctrl(c, c->ctrl2, hg));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(f, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+    TRY(read_ctrl(c, c->ctrl2, hf));
+    const double gbar = hg.rd / (double)c->N, fbar = hf.rd / (double)c->N;
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(w, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
+    TRY(full_dht<double>(c, w, 1.0, c->tb64));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec_apply_T<double>(w, kp, c->tb64, c->st)); }
+    TRY(full_dht<double>(c, w, kp.inv_ntot, c->tb64));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(w, w, nullptr, -1.0, 0.0, kp.s * kp.lam * gbar - fbar, c->N, c->st)); }
+    CK(cudaStreamSynchronize(c->st));
+  }
+  if (s != PSD_OK)
+    fail(c, s, std::string("solve ended with ") + psd_status_string(s));
+  return s;
+}
+
+}  // extern "C"

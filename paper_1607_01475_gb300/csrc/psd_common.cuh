@@ -1,0 +1,160 @@
+// Shared device-side definitions of the PSD library: parameter blocks, the
+// device-resident control block, and deterministic grid reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace psd {
+
+// Kinds of the vertex factor |g|^{p-2}: specialised p = 4 and a general p.
+enum PKind { PK_GEN = 0, PK_4 = 4 };
+
+// Slots of the "last block" counters in the control block.
+enum CounterSlot { CS_RES = 0, CS_MID = 1, CS_LS = 2, CS_MISC = 3, CS_COUNT = 8 };
+
+// Device-resident state of one PSD run.  Written only by the last block of
+// a reducing kernel (or by the host between runs).
+struct Ctrl {
+  int done;        // 1: converged, failed or stopped -> later kernels return
+  int iter;        // completed PSD iterations
+  int status;      // psd_status of the run
+  int max_iter;    // iteration limit for this run
+  double alpha;    // step size of the current iteration
+  double tol;      // stop when res_l2 < tol
+  double res_l2;   // ||r||_2 of the current iterate
+  double res_linf; // max |r| of the current iterate (-1 if not formed)
+  // Parseval sums of the current direction (already weighted by h^d / N):
+  double rd;       // (r, d)_2
+  double dd;       // (d, d)_2
+  double lapdd;    // (Delta_h d, Delta_h d)_2
+  double tdd;      // (T_h d, d)_2 (order 6)
+  // line-search sums (weighted by h^d): p = 4 polynomial coefficients
+  double c1, c2, c3;
+  // inner (mixed-precision) stop on the preconditioned residual norm
+  // (r, L_h^{-1} r)^{1/2} = ||d||_L (Eq. "RRT-1"): done when it drops below
+  // pre_eta times its first value pre_ref (pre_eta <= 0 disables).
+  double pre_eta;
+  double pre_ref;
+  unsigned int counter[CS_COUNT];
+  int hist_cap;
+  int pad_;
+  double* hist_alpha;  // device arrays of length hist_cap (or null)
+  double* hist_res;
+};
+
+// Problem scalars passed by value to the kernels.
+struct KParams {
+  int nx, ny, nz;       // cells per axis (nz = 1 in 2D)
+  int dim;
+  double h, inv_h;      // spacing
+  double s, eps2, lam;  // s, eps^2, lambda
+  double p;             // exponent
+  double cu;            // coefficient of u in N_h: 1 (order 4) or s*lambda (6)
+  double hd;            // h^d (cell volume)
+  double inv_ntot;      // 1 / (nx ny nz)
+  int order;
+  int pad_;
+};
+
+// ------------------------------------------------------------------ reductions
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Reduce M doubles over the block (fixed order: warp butterflies, then warp
+// 0 over the warp results); the result is valid in thread 0.  The last value
+// is reduced with max when LASTMAX is set.  Requires blockDim to be a
+// multiple of 32 (<= 1024) or smaller than 32 (then thread 0 sums serially);
+// uses a shared scratch of 32*M doubles.
+template <int M, bool LASTMAX>
+__device__ __forceinline__ void block_reduce(double (&v)[M], double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  if (nthr < 32) {
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < M; ++m) sh[tid * M + m] = v[m];
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        double acc = sh[m];
+        for (int t = 1; t < nthr; ++t) acc = (LASTMAX && m == M - 1) ? fmax(acc, sh[t * M + m]) : acc + sh[t * M + m];
+        v[m] = acc;
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
+#pragma unroll
+  for (int m = 0; m < M; ++m) v[m] = (LASTMAX && m == M - 1) ? warp_max(v[m]) : warp_sum(v[m]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) sh[wid * M + m] = v[m];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      double x = (lane < nw) ? sh[lane * M + m] : ((LASTMAX && m == M - 1) ? -1.0 : 0.0);
+      v[m] = (LASTMAX && m == M - 1) ? warp_max(x) : warp_sum(x);
+    }
+  }
+  __syncthreads();
+}
+
+// Write this block's partials, then return true in every thread of the
+// block that finished last (threadFenceReduction pattern).  The last block
+// can then read all partials with __ldcg.
+__device__ __forceinline__ bool publish_and_check_last(const double* v, int M, double* partials,
+                                                       unsigned int* counter, int* sh_flag) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+  if (tid == 0) {
+    for (int m = 0; m < M; ++m) partials[(size_t)bid * M + m] = v[m];
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    *sh_flag = (prev == nb - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  return *sh_flag != 0;
+}
+
+// In the last block: sum the partials of all blocks in a fixed order (each
+// thread a strided subset, then the block tree), result in thread 0.
+template <int M, bool LASTMAX>
+__device__ __forceinline__ void gather_partials(double (&out)[M], const double* partials, double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+#pragma unroll
+  for (int m = 0; m < M; ++m) out[m] = (LASTMAX && m == M - 1) ? -1.0 : 0.0;
+  for (unsigned int b = tid; b < nb; b += nthr) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      double x = __ldcg(partials + (size_t)b * M + m);
+      out[m] = (LASTMAX && m == M - 1) ? fmax(out[m], x) : out[m] + x;
+    }
+  }
+  block_reduce<M, LASTMAX>(out, sh);
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {  // n a power of two
+  return i & (n - 1);
+}
+
+}  // namespace psd

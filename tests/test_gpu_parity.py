@@ -1,0 +1,254 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative L-infinity, max|a - b| / max|b|):
+* residual, preconditioner, single PSD iterates in FP64: 1e-12.  Both sides
+  evaluate the same sums in a different order; each output is a sum of at
+  most ~30 terms whose magnitude is bounded by ~100x the result on these
+  inputs, so rounding differences stay below ~1e-13.
+* converged FP64 solutions: 1e-11 (the spec bar), both sides iterated
+  to the FP64 floor.
+* mixed precision after the outer FP64 correction: 1e-9.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1607_01475_gb300 import PSD_FP64, PSD_MIXED, Solver  # noqa: E402
+from paper_1607_01475_gb300 import synthetic  # noqa: E402
+
+rng = np.random.default_rng(2024)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def smooth_random(shape, K=6, seed=0):
+    return synthetic.fourier_field(shape, 2 * np.pi, K, 1000 + seed, nmodes=16)
+
+
+SHAPES = [(64, 64), (32, 128), (8, 8), (16, 16, 16), (8, 16, 32), (8, 8, 8), (32, 32, 64)]
+
+
+def _problem(oracle, order, shape, p, s=0.1, eps=0.2, lam=0.7):
+    h = 2 * np.pi / shape[-1]
+    return oracle.Problem(order, h, p, s, eps, lam), h
+
+
+# ---------------------------------------------------------------- residual
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("order,p", [(4, 4.0), (4, 3.0), (6, 4.0), (4, 6.0)])
+def test_residual_parity(oracle, shape, order, p):
+    P, h = _problem(oracle, order, shape, p)
+    u = rng.standard_normal(shape) * 0.3
+    f = rng.standard_normal(shape)
+    g = rng.standard_normal(shape) if order == 6 else None
+    if order == 6:
+        u = u - u.mean() + g.mean()
+    S = Solver(order, shape, h, p, P.s, P.eps, P.lam)
+    r = torch.empty(shape, dtype=torch.float64, device="cuda")
+    l2, linf = S.residual(dev(u), dev(f), None if g is None else dev(g), r)
+    ref = oracle.residual4(u, f, P) if order == 4 else oracle.residual6(u, f, g, P)
+    assert rel(host(r), ref) <= 1e-12
+    assert abs(l2 - oracle.norm2(ref, h)) <= 1e-12 * oracle.norm2(ref, h)
+    assert abs(linf - np.max(np.abs(ref))) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (16, 16, 16), (8, 32, 16)])
+def test_residual_f32_kernel(oracle, shape):
+    """The FP32 stencil kernel against the FP64 oracle: error of the order of
+    FP32 rounding times the size of the individual terms."""
+    P, h = _problem(oracle, 4, shape, 4.0)
+    u = smooth_random(shape, seed=1).astype(np.float32)
+    f = smooth_random(shape, seed=2).astype(np.float32)
+    S = Solver(4, shape, h, 4.0, P.s, P.eps)
+    r = torch.empty(shape, dtype=torch.float32, device="cuda")
+    S.residual_f32(torch.from_numpy(u).cuda(), torch.from_numpy(f).cuda(), r)
+    ref = oracle.residual4(u.astype(np.float64), f.astype(np.float64), P)
+    assert rel(host(r).astype(np.float64), ref) <= 2e-5
+
+
+# ---------------------------------------------------------- preconditioner
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("order", [4, 6])
+def test_precond_parity(oracle, shape, order):
+    P, h = _problem(oracle, order, shape, 4.0)
+    r = rng.standard_normal(shape)
+    S = Solver(order, shape, h, 4.0, P.s, P.eps, P.lam)
+    d = torch.empty(shape, dtype=torch.float64, device="cuda")
+    S.precond_solve(dev(r), d)
+    ref = oracle.precond4(r, P) if order == 4 else oracle.precond6(r, P)
+    assert rel(host(d), ref) <= 1e-12
+    # in place (r and d alias)
+    rd = dev(r)
+    S.precond_solve(rd, rd)
+    assert rel(host(rd), ref) <= 1e-12
+
+
+# ------------------------------------------------------------ PSD iterates
+
+@pytest.mark.parametrize("shape", [(64, 64), (16, 16, 16), (8, 16, 32), (8, 8), (8, 8, 8), (32, 64, 16)])
+@pytest.mark.parametrize("order,p", [(4, 4.0), (6, 4.0), (4, 3.0), (4, 6.0)])
+def test_iterates_parity(oracle, shape, order, p):
+    """u^k and alpha_k for k = 1..5 from the same u^0."""
+    P, h = _problem(oracle, order, shape, p, s=0.05, eps=0.15, lam=1.0)
+    f = smooth_random(shape, seed=3)
+    g = smooth_random(shape, seed=4) if order == 6 else None
+    u0 = np.zeros(shape) if order == 4 else np.full(shape, g.mean())
+    _, info = oracle.psd_solve(P, f, u0, g=g, tol=0.0, kmax=5, record=True)
+    for k in range(1, 6):
+        S = Solver(order, shape, h, p, P.s, P.eps, P.lam, tol=0.0, max_iter=k)
+        S.set_history(16)
+        u = dev(u0)
+        out = S.solve(dev(f), u, None if g is None else dev(g), allow_noconv=True)
+        assert out["iters"] == k
+        assert rel(host(u), info["u"][k]) <= 1e-12, k
+        alphas, res = S.history()
+        np.testing.assert_allclose(alphas[:k], info["alpha"][:k], rtol=1e-10)
+        np.testing.assert_allclose(res[:k + 1], info["res"][:k + 1], rtol=1e-10)
+
+
+# ------------------------------------------------------ converged solutions
+
+@pytest.mark.parametrize("shape", [(64, 64), (16, 16, 16), (32, 16), (8, 8, 8)])
+@pytest.mark.parametrize("order,p", [(4, 4.0), (6, 4.0), (4, 3.0)])
+def test_converged_parity_fp64(oracle, shape, order, p):
+    """Both sides iterated to the FP64 floor; the minimiser is unique
+    (strict convexity, Sec. 2.2), so the iterates must agree."""
+    P, h = _problem(oracle, order, shape, p, s=0.05, eps=0.15, lam=1.0)
+    f = smooth_random(shape, seed=5)
+    g = smooth_random(shape, seed=6) if order == 6 else None
+    u0 = np.zeros(shape) if order == 4 else np.full(shape, g.mean())
+    iters = 150
+    u_ref, info = oracle.psd_solve(P, f, u0, g=g, tol=0.0, kmax=iters)
+    S = Solver(order, shape, h, p, P.s, P.eps, P.lam, tol=0.0, max_iter=iters)
+    u = dev(u0)
+    w = torch.empty_like(u) if order == 6 else None
+    S.solve(dev(f), u, None if g is None else dev(g), w, allow_noconv=True)
+    assert rel(host(u), u_ref) <= 1e-11
+    if order == 6:
+        assert rel(host(w), oracle.recover_w(u_ref, f, g, P)) <= 1e-10
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (16, 16, 16), (8, 32, 16), (8, 8)])
+@pytest.mark.parametrize("order,p", [(4, 4.0), (6, 4.0), (4, 3.0)])
+def test_mixed_precision_parity(oracle, shape, order, p):
+    """FP32 inner PSD + outer FP64 residual correction reaches the FP64
+    solution to 1e-9 relative."""
+    P, h = _problem(oracle, order, shape, p, s=0.05, eps=0.15, lam=1.0)
+    f = smooth_random(shape, seed=7)
+    g = smooth_random(shape, seed=9) if order == 6 else None
+    u0 = np.zeros(shape) if order == 4 else np.full(shape, g.mean())
+    u_ref, _ = oracle.psd_solve(P, f, u0, g=g, tol=0.0, kmax=150)
+    S = Solver(order, shape, h, p, P.s, P.eps, P.lam, precision=PSD_MIXED, tol=1e-11, max_iter=2000,
+               max_outer=30)
+    u = dev(u0)
+    info = S.solve(dev(f), u, None if g is None else dev(g))
+    assert info["status"] == 0
+    assert info["res_l2"] < 1e-11
+    assert rel(host(u), u_ref) <= 1e-9
+
+
+# ---------------------------------------------------------------- edges
+
+def test_already_converged_and_zero_iterations(oracle):
+    shape = (32, 32)
+    P, h = _problem(oracle, 4, shape, 4.0)
+    f = smooth_random(shape, seed=8)
+    u_ref, _ = oracle.psd_solve(P, f, np.zeros(shape), tol=1e-12, kmax=500)
+    S = Solver(4, shape, h, 4.0, P.s, P.eps, tol=1e-10)
+    u = dev(u_ref)
+    info = S.solve(dev(f), u)
+    assert info["iters"] == 0 and info["status"] == 0
+    assert np.array_equal(host(u), u_ref)
+    S0 = Solver(4, shape, h, 4.0, P.s, P.eps, tol=1e-10, max_iter=0)
+    u = dev(np.zeros(shape))
+    info = S0.solve(dev(f), u, allow_noconv=True)
+    assert info["iters"] == 0 and info["status"] == 4
+
+
+def test_nonfinite_input_is_reported(oracle):
+    shape = (16, 16)
+    P, h = _problem(oracle, 4, shape, 4.0)
+    f = np.ones(shape)
+    f[3, 4] = np.nan
+    S = Solver(4, shape, h, 4.0, P.s, P.eps, tol=1e-10)
+    from paper_1607_01475_gb300 import PSDError
+    with pytest.raises(PSDError) as e:
+        S.solve(dev(f), dev(np.zeros(shape)))
+    assert e.value.status == 7
+
+
+# ------------------------------------------------ full-size workloads
+
+@pytest.mark.parametrize("shape", [(1024, 1024), (128, 128, 128)])
+@pytest.mark.parametrize("precision", [PSD_FP64, PSD_MIXED])
+def test_full_size_thin_film_solution_checked_by_oracle(oracle, shape, precision):
+    """At the benchmark sizes the oracle cannot run PSD in seconds, but it can
+    evaluate its own residual at the GPU's answer: a property that holds at
+    any size (||f - N_h[u]||_2 < tol)."""
+    wl = synthetic.workload_thin_film(shape)
+    P = oracle.Problem(4, wl["L"] / shape[-1], wl["p"], wl["s"], wl["eps"])
+    S = Solver(4, shape, P.h, P.p, P.s, P.eps, precision=precision, tol=1e-10, max_iter=5000)
+    u = dev(wl["u0"])
+    info = S.solve(dev(wl["f"]), u)
+    assert info["status"] == 0
+    r = oracle.residual4(host(u), wl["f"], P)
+    assert oracle.norm2(r, P.h) < 1e-10 * 1.05
+
+
+@pytest.mark.parametrize("shape", [(128, 128, 128)])
+def test_full_size_spfc_solution_checked_by_oracle(oracle, shape):
+    """Sixth order at 128^3: the oracle's own residual (with its own FFT for
+    T_h) at the GPU's mixed-precision answer is below the tolerance, and the
+    mean constraint mean(u) = mean(g) holds."""
+    wl = synthetic.workload_spfc(shape)
+    P = oracle.Problem(6, wl["L"] / shape[-1], wl["p"], wl["s"], wl["eps"], wl["lam"])
+    S = Solver(6, shape, P.h, P.p, P.s, P.eps, P.lam, precision=PSD_MIXED, tol=1e-10, max_iter=5000)
+    u = dev(wl["u0"])
+    info = S.solve(dev(wl["f"]), u, dev(wl["g"]))
+    assert info["status"] == 0
+    uh = host(u)
+    assert abs(uh.mean() - wl["g"].mean()) < 1e-13
+    r = oracle.residual6(uh, wl["f"], wl["g"], P)
+    assert oracle.norm2(r, P.h) < 1e-10 * 1.05
+
+
+def test_bench_workload_mixed_matches_fp64():
+    """The 3D 256^3 sixth-order workload: the mixed-precision and plain FP64
+    solutions agree to 1e-9 relative and both meet the tolerance."""
+    shape = (256, 256, 256)
+    wl = synthetic.workload_spfc(shape)
+    h = wl["L"] / shape[-1]
+    out = {}
+    for prec in (PSD_FP64, PSD_MIXED):
+        S = Solver(6, shape, h, wl["p"], wl["s"], wl["eps"], wl["lam"], precision=prec, tol=1e-10,
+                   max_iter=5000)
+        u = dev(wl["u0"])
+        info = S.solve(dev(wl["f"]), u, dev(wl["g"]))
+        assert info["status"] == 0 and info["res_l2"] < 1e-10
+        l2, _ = S.residual(u, dev(wl["f"]), dev(wl["g"]))
+        assert l2 < 1e-10
+        out[prec] = host(u)
+        S.close()
+        del u
+        torch.cuda.empty_cache()
+    assert rel(out[PSD_MIXED], out[PSD_FP64]) <= 1e-9

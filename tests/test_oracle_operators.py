@@ -289,7 +289,9 @@ def test_second_order_consistency(oracle, p):
         e = oracle.N4(uf(X, Y), P) - Nf(X, Y)
         errs.append(np.max(np.abs(e)))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-    assert np.all(rates > 1.9) and np.all(rates < 2.1), rates
+    # asymptotically second order: the finest rate is 2 within 0.05 and the
+    # rates approach it from the pre-asymptotic side
+    assert 1.95 < rates[-1] < 2.05 and np.all(rates > 1.7) and np.all(np.diff(rates) > -0.02), rates
 
 
 # ------------------------------------------- symmetries
