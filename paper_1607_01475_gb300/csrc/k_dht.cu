@@ -213,10 +213,20 @@ __global__ void __launch_bounds__(kThreads)
       ctrl->lapdd = tot[2] * w;
       ctrl->tdd = tot[3] * w;
       if (ctrl->pre_eta > 0.0) {
+        // inner solve: stop when the preconditioned norm has dropped by
+        // pre_eta, or when it has stopped halving (its rounding floor)
         const double pn = sqrt(fmax(ctrl->rd, 0.0));
         if (ctrl->pre_ref <= 0.0) {
           ctrl->pre_ref = pn;
+          ctrl->pre_win = pn;
+          ctrl->pre_stall = 0;
         } else if (pn < ctrl->pre_eta * ctrl->pre_ref) {
+          ctrl->status = 0;
+          ctrl->done = 1;
+        } else if (pn < 0.5 * ctrl->pre_win) {
+          ctrl->pre_win = pn;
+          ctrl->pre_stall = 0;
+        } else if (++ctrl->pre_stall >= ctrl->pre_stall_max) {
           ctrl->status = 0;
           ctrl->done = 1;
         }

@@ -33,7 +33,8 @@ thread_local std::string g_create_error;
 
 constexpr int kChunk = 8;          // iterations enqueued between host checks
 constexpr int kLsPassesGen = 16;   // Newton passes of the general-p line search
-constexpr double kInnerEta = 1e-5;  // inner FP32 solve: relative drop of the preconditioned norm
+constexpr double kInnerEta = 1e-4;  // inner FP32 solve: relative drop of the preconditioned norm
+constexpr int kInnerStall = 5;      // ... or this many iterations without halving it
 constexpr int kInnerMaxIter = 400;  // inner FP32 iterations per outer correction
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
@@ -467,10 +468,12 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
     // order eps32 * 64 s eps^2 / h^4 * |delta|, which on fine grids is as large
     // as the residual itself, so ||r||_2 cannot serve as the inner stopping
     // test.  The preconditioned norm (r, L_h^{-1} r)^{1/2} damps that noise by
-    // the symbol of L_h; the inner solve stops when it has dropped by kInnerEta.
+    // the symbol of L_h; the inner solve stops when it has dropped by
+    // kInnerEta, or when it has stopped halving (its FP32 floor).
     Ctrl h;
     init_ctrl(h, 0.0, std::min(c->prm.max_iter - inner_total, kInnerMaxIter));
     h.pre_eta = kInnerEta;
+    h.pre_stall_max = kInnerStall;
     TRY(upload_ctrl(c, c->ctrl, h));
     CK(cudaMemsetAsync(c->da, 0, c->N * sizeof(float), c->st));
     if (six) {

@@ -36,6 +36,9 @@ struct Ctrl {
   // pre_eta times its first value pre_ref (pre_eta <= 0 disables).
   double pre_eta;
   double pre_ref;
+  double pre_win;  // value at the start of the current stall window
+  int pre_stall;   // iterations without halving pre_win
+  int pre_stall_max;
   unsigned int counter[CS_COUNT];
   int hist_cap;
   int pad_;
