@@ -153,6 +153,29 @@ psd_status psd_profile_read(psd_handle h, double* ms, long long* launches,
 /* Static name of a kernel class ("residual_fp64", ...), or NULL.           */
 const char* psd_profile_class_name(int k);
 
+/* Fourth-order FP64 residual r = f - N_h[u] with ||r||_2 and max|r| (as
+ * psd_residual), without a handle and without allocating any device memory.
+ * The paper has no counterpart; this exists for callers that must not call
+ * cudaMalloc -- code running during stream capture under an allocator that
+ * refuses new allocations, plug-ins whose host application owns every device
+ * allocation, and fixed-budget deployments.  The kernel's scratch (block
+ * partial sums and the reduction control block) is a file-scope __device__
+ * array of about 33 KB that every GPU loading the library keeps until exit.
+ * params: order must be 4; its stream is used; tol, max_iter, max_outer and
+ * precision are ignored.  u, f, r: device arrays as for psd_residual (r is
+ * required); res_l2 / res_linf: host pointers or NULL.  Synchronises the
+ * stream.  Returns PSD_ERR_INVALID for a bad size or parameter, including
+ * grids whose residual launch needs more than 2048 blocks (beyond 256^3 in
+ * 3D; every 2D size up to 1024^2 fits).  All calls share the scratch: calls
+ * that overlap on the GPU race.  The first call on a device looks up the
+ * scratch address; make it before any stream capture.                    */
+psd_status psd_residual_noalloc(const psd_params* params, const double* u,
+                                const double* f, double* r, double* res_l2,
+                                double* res_linf);
+
+/* Text of the last error of psd_residual_noalloc in this host thread.     */
+psd_status psd_noalloc_last_error(char* buf, size_t len);
+
 /* Text of the last error on this handle (or of the last psd_create failure
  * when h is NULL), copied into buf (always NUL-terminated).                */
 psd_status psd_last_error(psd_handle h, char* buf, size_t len);

@@ -74,11 +74,14 @@ def load_library(build_if_missing=True):
     lib.psd_profile_read.argtypes = [H, P, P, P, P, ctypes.c_double, ctypes.c_int]
     lib.psd_profile_class_name.argtypes = [ctypes.c_int]
     lib.psd_profile_class_name.restype = ctypes.c_char_p
+    lib.psd_residual_noalloc.argtypes = [ctypes.POINTER(PSDParams), D, D, D, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]
+    lib.psd_noalloc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     lib.psd_status_string.argtypes = [ctypes.c_int]
     lib.psd_status_string.restype = ctypes.c_char_p
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
                  "psd_set_history", "psd_residual_f32", "psd_last_error", "psd_profile",
-                 "psd_profile_read"):
+                 "psd_profile_read", "psd_residual_noalloc", "psd_noalloc_last_error"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -156,6 +159,24 @@ def psd_solve(handle, f, u, g=None, w=None, allow_noconv=False):
 def psd_residual_f32(handle, u, f, r):
     _check(load_library().psd_residual_f32(handle, _ptr(u, "float32"), _ptr(f, "float32"),
                                            _ptr(r, "float32")), handle)
+
+
+def psd_residual_noalloc(shape, h, p, s, eps, u, f, r, stream=None):
+    """Fourth-order residual and norms without a handle or any device
+    allocation (see include/psd.h).  Returns (||r||_2, max|r|)."""
+    lib = load_library()
+    dim = len(shape)
+    n = (shape[-1], shape[-2], shape[0] if dim == 3 else 1)
+    prm = PSDParams(order=4, dim=dim, n=(ctypes.c_int * 3)(*n), h=h, p=p, s=s, eps=eps, lam=0.0,
+                    precision=0, tol=0.0, max_iter=0, max_outer=0, stream=_stream_handle(stream))
+    l2, linf = ctypes.c_double(), ctypes.c_double()
+    st = lib.psd_residual_noalloc(ctypes.byref(prm), _ptr(u), _ptr(f), _ptr(r), ctypes.byref(l2),
+                                  ctypes.byref(linf))
+    if st != 0:
+        buf = ctypes.create_string_buffer(256)
+        lib.psd_noalloc_last_error(buf, len(buf))
+        raise PSDError(st, buf.value.decode())
+    return l2.value, linf.value
 
 
 # ------------------------------------------------------------- convenience

@@ -672,6 +672,17 @@ cudaError_t launch_residual(const ResArgs<T>& a, int mode, int pk, const KParams
   return res_impl<T, PK_GEN, RM_PLAIN>(a, kp, ctrl, partials, st);
 }
 
+long long residual_grid_blocks(const KParams& kp) {
+  if (kp.dim == 3) {
+    const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY3 ? kp.ny : BY3;
+    const int gx = kp.nx / TX, gy = kp.ny / TY;
+    const int zc = pick_zc(kp.nz, gx * gy);
+    return (long long)gx * gy * (kp.nz / zc);
+  }
+  const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY2 ? kp.ny : BY2;
+  return (long long)(kp.nx / TX) * (kp.ny / TY);
+}
+
 template <typename T>
 cudaError_t launch_linesearch(const T* u, const T* ubase, const T* d, int pk, const KParams& kp, Ctrl* ctrl,
                               double* partials, cudaStream_t st) {

@@ -75,6 +75,10 @@ template <typename T>
 cudaError_t launch_linesearch(const T* u, const T* ubase, const T* d, int pk, const KParams& kp,
                               Ctrl* ctrl, double* partials, cudaStream_t st);
 
+// Number of blocks launch_residual uses for this problem size (one partial
+// sum record per block).
+long long residual_grid_blocks(const KParams& kp);
+
 // ------------------------------------------------------------------ misc
 // y = a * x + b * z + c elementwise (x or z may be null = 0; may alias y).
 template <typename T>

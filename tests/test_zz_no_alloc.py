@@ -1,0 +1,68 @@
+"""psd_residual_noalloc: the allocation-free residual entry point.
+
+It serves callers that cannot call cudaMalloc (stream capture under an
+allocator that refuses new allocations, plug-ins whose host owns every device
+allocation, fixed-budget deployments).  Its scratch is a static __device__
+array, so these tests check that it gives the same residual and norms as the
+handle-based psd_residual, on consecutive calls (the scratch keeps the last
+call's contents and must be cleared by each call), and that sizes beyond the
+array are refused.  The file is named so that pytest collects it last.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1607_01475_gb300 import PSDError, Solver, psd_residual_noalloc  # noqa: E402
+from paper_1607_01475_gb300 import _lib  # noqa: E402
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("shape,p", [((64, 64), 4.0), ((32, 32, 32), 4.0), ((16, 32, 64), 3.0),
+                                     ((1024, 1024), 4.0), ((256, 256, 256), 4.0)])
+def test_noalloc_matches_handle_residual_on_consecutive_calls(shape, p):
+    rng = np.random.default_rng(11)
+    h = 2 * np.pi / shape[-1]
+    s, eps = 0.1, 0.2
+    u = torch.from_numpy(rng.standard_normal(shape) * 0.3).cuda()
+    f = torch.from_numpy(rng.standard_normal(shape)).cuda()
+    S = Solver(4, shape, h, p, s, eps)
+    r_ref = torch.empty_like(u)
+    l2_ref, linf_ref = S.residual(u, f, None, r_ref)
+    ref = r_ref.cpu().numpy()
+    for call in range(2):
+        r = torch.full_like(u, float("nan"))
+        l2, linf = psd_residual_noalloc(shape, h, p, s, eps, u, f, r)
+        assert _rel(r.cpu().numpy(), ref) <= 1e-12, call
+        assert abs(l2 - l2_ref) <= 1e-12 * l2_ref, call
+        assert abs(linf - linf_ref) <= 1e-12 * linf_ref, call
+    S.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    shape = (8, 1024, 1024)  # needs 4096 residual blocks; the scratch holds 2048
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    r = torch.empty_like(u)
+    with pytest.raises(PSDError) as e:
+        psd_residual_noalloc(shape, 0.01, 4.0, 0.1, 0.1, u, u, r)
+    assert e.value.status == 1
+    assert "scratch" in str(e.value)
+
+
+def test_noalloc_rejects_sixth_order():
+    lib = _lib.load_library()
+    prm = _lib.PSDParams(order=6, dim=2, n=(ctypes.c_int * 3)(64, 64, 1), h=0.1, p=4.0, s=0.1, eps=0.1,
+                         lam=1.0, precision=0, tol=0.0, max_iter=0, max_outer=0, stream=None)
+    x = torch.zeros((64, 64), dtype=torch.float64, device="cuda")
+    ptr = ctypes.c_void_p(x.data_ptr())
+    assert lib.psd_residual_noalloc(ctypes.byref(prm), ptr, ptr, ptr, None, None) == 1
