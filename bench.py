@@ -107,11 +107,14 @@ class ClockSampler:
 # sixth-order path (reads + writes of whole fields, in the class precision).
 def algorithmic_bytes_per_cell(cls, order):
     w = 8 if cls.endswith("fp64") else 4
+    fp32 = cls.endswith("fp32")
     table = {
-        "residual": 6 if cls.endswith("fp32") else 5,   # inner: delta, d, R, ubase in; delta', r out
+        # inner (order 6): delta, d, ubase in; delta', r out.  FP64 plain: u, d, f in; u', r out
+        "residual": (5 if order == 6 else 6) if fp32 else 5,
         "dht_rows": 2, "dht_cols": 2,
-        "mid": 6 if order == 6 else 2,                   # W, zeta, dspec in and out
-        "linesearch": 3 if cls.endswith("fp32") else 2,  # delta, ubase, d  /  u, d
+        # order 6: W, zeta, dspec (+ the outer residual's spectrum in the inner solve) in; W, zeta, dspec out
+        "mid": (7 if fp32 else 6) if order == 6 else 2,
+        "linesearch": 3 if fp32 else 2,  # delta, ubase, d  /  u, d
     }
     base = cls.rsplit("_", 1)[0]
     return table.get(base, 0) * w

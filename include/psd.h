@@ -112,6 +112,29 @@ psd_status psd_precond_solve(psd_handle h, const double* r, double* d);
 psd_status psd_solve(psd_handle h, const double* f, const double* g,
                      double* u, double* w, psd_info* info);
 
+/* Hessian-vector product y = H v, H = dN_h/du at u (the second variation of
+ * E_h, Sec. 5.3, in the Euclidean product): H v = v - s grad_h^v.(W(Du) Dv)
+ * + s eps^2 Delta_h^2 v with W(g) = |g|^{p-2} I + (p-2)|g|^{p-4} g g^T.
+ * Order 4, FP64, device arrays; synchronises the stream.  dot (host, may be
+ * NULL) receives h^d sum v.y.                                             */
+psd_status psd_hvp(psd_handle h, const double* u, const double* v, double* y,
+                   double* dot);
+
+/* Gradient of a loss J(u) of the converged solution u of N_h[u] = f with
+ * respect to f and s (order 4).  Not in the paper: by the implicit function
+ * theorem, H lambda = grad_u (H symmetric, solved by conjugate gradients
+ * preconditioned with the FFT solve of L_h), grad_f = lambda and
+ * grad_s = -sum_i lambda_i (dN_h/ds)_i, dN_h/ds = -grad_h^v.(|Du|^{p-2}Du)
+ * + eps^2 Delta_h^2 u.  u, grad_u: device arrays (grad_u = dJ/du entrywise);
+ * grad_f: device output (may alias grad_u); grad_s: host double (may be
+ * NULL).  The solve stops when ||r||_2 <= tol_rel ||grad_u||_2 (tol_rel <= 0
+ * selects 1e-12) or after max_iter iterations (PSD_ERR_NOCONV).  info (may
+ * be NULL): iters = CG iterations, res_l2 = final relative residual.  Uses
+ * the handle's workspace; synchronises the stream.                        */
+psd_status psd_adjoint(psd_handle h, const double* u, const double* grad_u,
+                       double* grad_f, double* grad_s, double tol_rel,
+                       int max_iter, psd_info* info);
+
 /* Record per-iteration step sizes alpha_k and residual norms ||r_k||_2 of
  * subsequent psd_solve calls into host arrays of capacity cap (both may be
  * NULL to stop recording).  res_hist[0] is ||r_0||.                        */

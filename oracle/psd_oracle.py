@@ -55,7 +55,7 @@ __all__ = [
     "ip2", "ipv", "norm2", "mu_symbol",
     "N4", "residual4", "energy4", "second_variation4", "precond4",
     "T_h", "N6", "residual6", "energy6", "second_variation6", "precond6",
-    "recover_w", "line_search", "psd_solve", "Problem",
+    "recover_w", "line_search", "psd_solve", "Problem", "hvp4", "dN4_ds", "adjoint4",
 ]
 
 
@@ -493,3 +493,62 @@ def psd_solve(P, f, u0, g=None, tol=1e-10, kmax=1000, record=False):
         if info["res"][-1] < tol:
             break
     return u, info
+
+
+# --------------------------------------------------------------------------
+# Adjoint (gradient of a loss of the converged solution).  Not in the paper:
+# by the implicit function theorem at the solution of N_h[u] = f,
+#   dJ/df = lambda,  dJ/ds = -(lambda . dN_h/ds),  H lambda = dJ/du,
+# with H = dN_h/du (the array Jacobian, symmetric: h^{-d} times the Hessian
+# of E_h, i.e. the second variation of Sec. 5.3 in the Euclidean product).
+# Gradients are with respect to the array entries (Euclidean).
+# --------------------------------------------------------------------------
+
+def hvp4(u, v, P):
+    """H v = v - s d.(W(g) D v) + s eps^2 Delta_h^2 v with g = D u and
+    W(g) = |g|^{p-2} I + (p-2)|g|^{p-4} g g^T (second variation, Sec. 5.3;
+    the (p-2)-term is 0 where g = 0 for p < 4)."""
+    h = P.h
+    g = vgrad(u, h)
+    b = vgrad(v, h)
+    g2 = sum(c * c for c in g)
+    gb = sum(c * e for c, e in zip(g, b))
+    r = _vertex_factor(g2, P.p)
+    if P.p == 2:
+        w = 0.0 * g2
+    else:
+        with np.errstate(divide="ignore", invalid="ignore"):
+            w = np.where(g2 > 0, (P.p - 2.0) * g2 ** ((P.p - 4.0) / 2.0) * gb, 0.0)
+    flux = [r * e + w * c for c, e in zip(g, b)]
+    return v - P.s * vdiv(flux, h) + P.s * P.eps ** 2 * lap(lap(v, h), h)
+
+
+def dN4_ds(u, P):
+    """Partial derivative of N_h[u] with respect to s."""
+    h = P.h
+    return -plap(u, h, P.p) + P.eps ** 2 * lap(lap(u, h), h)
+
+
+def adjoint4(u, grad_u, P, tol=1e-13, kmax=2000):
+    """Solve H lam = grad_u by conjugate gradients preconditioned with L_h
+    (the PSD preconditioner); return (grad_f, grad_s, iterations)."""
+    lam = np.zeros_like(grad_u)
+    r = grad_u.copy()
+    z = precond4(r, P)
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    bnorm = np.sqrt(float(np.sum(grad_u * grad_u)))
+    it = 0
+    for it in range(1, kmax + 1):
+        Hp = hvp4(u, p, P)
+        a = rz / float(np.sum(p * Hp))
+        lam = lam + a * p
+        r = r - a * Hp
+        if np.sqrt(float(np.sum(r * r))) <= tol * bnorm:
+            break
+        z = precond4(r, P)
+        rz_new = float(np.sum(r * z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    grad_s = -float(np.sum(lam * dN4_ds(u, P)))
+    return lam, grad_s, it

@@ -74,6 +74,9 @@ def load_library(build_if_missing=True):
     lib.psd_profile_read.argtypes = [H, P, P, P, P, ctypes.c_double, ctypes.c_int]
     lib.psd_profile_class_name.argtypes = [ctypes.c_int]
     lib.psd_profile_class_name.restype = ctypes.c_char_p
+    lib.psd_hvp.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
+    lib.psd_adjoint.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int,
+                                ctypes.POINTER(PSDInfo)]
     lib.psd_residual_noalloc.argtypes = [ctypes.POINTER(PSDParams), D, D, D, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     lib.psd_noalloc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -81,7 +84,8 @@ def load_library(build_if_missing=True):
     lib.psd_status_string.restype = ctypes.c_char_p
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
                  "psd_set_history", "psd_residual_f32", "psd_last_error", "psd_profile",
-                 "psd_profile_read", "psd_residual_noalloc", "psd_noalloc_last_error"):
+                 "psd_profile_read", "psd_residual_noalloc", "psd_noalloc_last_error", "psd_hvp",
+                 "psd_adjoint"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -156,6 +160,22 @@ def psd_solve(handle, f, u, g=None, w=None, allow_noconv=False):
     return info.as_dict()
 
 
+def psd_hvp(handle, u, v, y):
+    """y = H v (Hessian of the discrete energy at u, Euclidean); returns h^d v.y."""
+    dot = ctypes.c_double()
+    _check(load_library().psd_hvp(handle, _ptr(u), _ptr(v), _ptr(y), ctypes.byref(dot)), handle)
+    return dot.value
+
+
+def psd_adjoint(handle, u, grad_u, grad_f, tol_rel=1e-12, max_iter=1000):
+    """grad_f <- dJ/df; returns (dJ/ds, info)."""
+    gs = ctypes.c_double()
+    info = PSDInfo()
+    _check(load_library().psd_adjoint(handle, _ptr(u), _ptr(grad_u), _ptr(grad_f), ctypes.byref(gs),
+                                      tol_rel, max_iter, ctypes.byref(info)), handle)
+    return gs.value, info.as_dict()
+
+
 def psd_residual_f32(handle, u, f, r):
     _check(load_library().psd_residual_f32(handle, _ptr(u, "float32"), _ptr(f, "float32"),
                                            _ptr(r, "float32")), handle)
@@ -228,6 +248,12 @@ class Solver:
 
     def solve(self, f, u, g=None, w=None, allow_noconv=False):
         return psd_solve(self.handle, f, u, g, w, allow_noconv)
+
+    def hvp(self, u, v, y):
+        return psd_hvp(self.handle, u, v, y)
+
+    def adjoint(self, u, grad_u, grad_f, tol_rel=1e-12, max_iter=1000):
+        return psd_adjoint(self.handle, u, grad_u, grad_f, tol_rel, max_iter)
 
     def profile(self, enable=True):
         _check(load_library().psd_profile(self.handle, 1 if enable else 0), self.handle)

@@ -93,10 +93,16 @@ struct DFT<1> {
 // transform in natural order in sr/si (shared memory, length N), visible to
 // the whole block on return.  Every thread of the block must call this
 // (it contains __syncthreads).  twc/tws: cos/sin(2 pi t / N), t < N.
-template <typename T, int N>
+template <typename T, int N, int RMAX = 16>
 struct LineFFT {
-  static constexpr int R = N < 16 ? N : 16;
+  static_assert(RMAX == 2 || RMAX == 4 || RMAX == 8 || RMAX == 16, "radix must divide 16");
+  static constexpr int R = N < RMAX ? N : RMAX;
   static constexpr int TS = N / R;
+  // Shared-memory index of point i: one padding word every 16 points, so
+  // that the radix-R scatter of the first pass (stride R) and the strided
+  // gathers hit distinct banks.  A line occupies L = N + N/16 words.
+  static constexpr int L = N + N / 16;
+  __device__ __forceinline__ static int pix(int i) { return i + (i >> 4); }
 
   template <int NS>
   __device__ __forceinline__ static void pass(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si,
@@ -127,8 +133,8 @@ struct LineFFT {
       const int base = (jp / NS) * NS * RP + jm;
 #pragma unroll
       for (int r = 0; r < RP; ++r) {
-        sr[base + r * NS] = xr[r];
-        si[base + r * NS] = xi[r];
+        sr[pix(base + r * NS)] = xr[r];
+        si[pix(base + r * NS)] = xi[r];
       }
     }
   }
@@ -141,8 +147,8 @@ struct LineFFT {
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        vr[q] = sr[j + q * TS];
-        vi[q] = si[j + q * TS];
+        vr[q] = sr[pix(j + q * TS)];
+        vi[q] = si[pix(j + q * TS)];
       }
       __syncthreads();
       pass<NS>(vr, vi, j, sr, si, twc, tws);
@@ -158,11 +164,13 @@ struct LineFFT {
   }
 };
 
-// Hartley outputs of the two real lines packed in a complex spectrum.
+// Hartley outputs of the two real lines packed in a complex spectrum (the
+// line stored with the padded index i + i/16).
 template <typename T>
 __device__ __forceinline__ void dht_split(const T* sr, const T* si, int k, int N, T& h1, T& h2) {
   const int k2 = (N - k) & (N - 1);
-  const T A = sr[k], B = si[k], C = sr[k2], D = si[k2];
+  const int a = k + (k >> 4), b = k2 + (k2 >> 4);
+  const T A = sr[a], B = si[a], C = sr[b], D = si[b];
   h1 = T(0.5) * ((A - B) + (C + D));
   h2 = T(0.5) * ((A + B) - (C - D));
 }

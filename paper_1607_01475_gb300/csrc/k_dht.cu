@@ -21,16 +21,25 @@ struct Vec2<double> {
   using type = double2;
 };
 
-constexpr int PAD = 1;
 constexpr int kThreads = 256;
+
+// Words between the real arrays of consecutive column pairs in shared memory
+// (each pair holds its real and imaginary line of F::L words).  Row passes
+// put two pairs in a warp and want the pair offset at 16 banks (stride = 8
+// mod 16); column passes put many pairs in a warp and want consecutive pairs
+// 2 banks apart (stride = 1 mod 16).
+template <int L, bool ROWS>
+__host__ __device__ constexpr int line_stride_words() {
+  return ROWS ? L + ((8 - (L & 15)) & 15) : L + ((1 - (L & 15)) & 15);
+}
 constexpr size_t kMaxSmem = 96 * 1024;
 
 // -------------------------------------------------------------- x (rows)
-template <typename T, int N>
+template <typename T, int N, int RM>
 __global__ void __launch_bounds__(kThreads)
     k_dht_rows(const T* src, T* dst, int nrows, T scale, const int* done, const T* __restrict__ twc,
                const T* __restrict__ tws) {
-  using F = LineFFT<T, N>;
+  using F = LineFFT<T, N, RM>;
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -39,8 +48,9 @@ __global__ void __launch_bounds__(kThreads)
   const int p = tid / F::TS, j = tid - p * F::TS;
   const int row0 = 2 * (blockIdx.x * pairs + p);
   const bool valid = row0 < nrows;
-  T* sr = sm + (size_t)p * 2 * (N + PAD);
-  T* si = sr + (N + PAD);
+  constexpr int LS = line_stride_words<F::L, true>();
+  T* sr = sm + (size_t)p * 2 * LS;
+  T* si = sr + LS;
   T vr[F::R], vi[F::R];
   const T* s0 = src + (size_t)row0 * N;
 #pragma unroll
@@ -66,11 +76,11 @@ __global__ void __launch_bounds__(kThreads)
 // Block: `pairs` pairs of adjacent x-columns (x, x+1) packed as re/im, lines
 // along the strided axis; thread (p, j) = (tid % pairs, tid / pairs) so that a
 // warp reads whole row segments.
-template <typename T, int N>
+template <typename T, int N, int RM>
 __global__ void __launch_bounds__(kThreads)
     k_dht_cols(T* data, size_t line_stride, size_t outer_stride, T scale, const int* done,
                const T* __restrict__ twc, const T* __restrict__ tws) {
-  using F = LineFFT<T, N>;
+  using F = LineFFT<T, N, RM>;
   using V = typename Vec2<T>::type;
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -79,8 +89,9 @@ __global__ void __launch_bounds__(kThreads)
   const int pairs = blockDim.x / F::TS;
   const int p = tid % pairs, j = tid / pairs;
   const size_t base = (size_t)blockIdx.y * outer_stride + (size_t)blockIdx.x * 2 * pairs + 2 * p;
-  T* sr = sm + (size_t)p * 2 * (N + PAD);
-  T* si = sr + (N + PAD);
+  constexpr int LS = line_stride_words<F::L, false>();
+  T* sr = sm + (size_t)p * 2 * LS;
+  T* si = sr + LS;
   T vr[F::R], vi[F::R];
 #pragma unroll
   for (int q = 0; q < F::R; ++q) {
@@ -102,25 +113,26 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ------------------------------------------------------------- middle pass
-template <typename T, int N, int ORDER>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, int N, int ORDER, int RM>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
     k_mid(T* data, size_t line_stride, size_t outer_stride, KParams kp, Ctrl* ctrl, double* partials,
-          T* zeta, T* dspec, const T* __restrict__ symx, const T* __restrict__ symo,
+          T* xi, T* dspec, const T* __restrict__ symx, const T* __restrict__ symo,
           const T* __restrict__ syml, const T* __restrict__ twc, const T* __restrict__ tws) {
-  using F = LineFFT<T, N>;
+  using F = LineFFT<T, N, RM>;
   using V = typename Vec2<T>::type;
   if (ctrl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  __shared__ double sred[32 * 5];
+  __shared__ T sred[32 * 5];
   __shared__ int sflag;
   const int tid = threadIdx.x;
   const int pairs = blockDim.x / F::TS;
   const int p = tid % pairs, j = tid / pairs;
   const int x = blockIdx.x * 2 * pairs + 2 * p;
   const size_t base = (size_t)blockIdx.y * outer_stride + x;
-  T* sr = sm + (size_t)p * 2 * (N + PAD);
-  T* si = sr + (N + PAD);
+  constexpr int LS = line_stride_words<F::L, false>();
+  T* sr = sm + (size_t)p * 2 * LS;
+  T* si = sr + LS;
   T vr[F::R], vi[F::R];
 #pragma unroll
   for (int q = 0; q < F::R; ++q) {
@@ -154,32 +166,40 @@ __global__ void __launch_bounds__(kThreads)
         acc[2] += (mu * dd) * (mu * dd);
       }
     } else {
+      // xi holds the transformed part of the residual that is linear in the
+      // iterate and not formed by the stencil kernel: -T_h[u - g] (plain
+      // FP64) or R_outer - T_h[delta] (inner solve); it advances with the
+      // previous step, xi -= alpha_prev T_h d_prev = alpha_prev dspec / mu.
       const size_t idx = base + (size_t)k * line_stride;
-      V z = *reinterpret_cast<const V*>(zeta + idx);
+      const V xv = *reinterpret_cast<const V*>(xi + idx);
       const V dp = *reinterpret_cast<const V*>(dspec + idx);
-      z.x += alpha_prev * dp.x;
-      z.y += alpha_prev * dp.y;
-      *reinterpret_cast<V*>(zeta + idx) = z;
-      const T zz[2] = {z.x, z.y};
+      const T xs[2] = {xv.x, xv.y}, ds[2] = {dp.x, dp.y};
+      T xn[2];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const T mu = (c ? mxb : mxa) + ml;
-        T rt = T(0), dd = T(0);
+        T rt = T(0), dd = T(0), xc = T(0);
         if (mu > T(0)) {
-          rt = h[c] - zz[c] / mu;
-          const T L = sl + s * mu + se2 * mu * mu + T(1) / mu;
+          const T imu = T(1) / mu;
+          xc = xs[c] - alpha_prev * ds[c] * imu;
+          rt = h[c] + xc;
+          const T L = sl + s * mu + se2 * mu * mu + imu;
           dd = rt / L;
-          acc[3] += dd * dd / mu;
+          acc[3] += dd * dd * imu;
         }
+        xn[c] = xc;
         dv[c] = dd;
         acc[0] += rt * dd;
         acc[1] += dd * dd;
         acc[2] += (mu * dd) * (mu * dd);
         acc[4] += rt * rt;
       }
-      V o;
+      V xo, o;
+      xo.x = xn[0];
+      xo.y = xn[1];
       o.x = dv[0];
       o.y = dv[1];
+      *reinterpret_cast<V*>(xi + idx) = xo;
       *reinterpret_cast<V*>(dspec + idx) = o;
     }
     vr[q] = dv[0];
@@ -199,13 +219,15 @@ __global__ void __launch_bounds__(kThreads)
     *reinterpret_cast<V*>(data + base + (size_t)k * line_stride) = o;
   }
 
-  double v[5];
+  T v[5];
 #pragma unroll
-  for (int m = 0; m < 5; ++m) v[m] = (double)acc[m];
-  block_reduce<5, false>(v, sred);
-  if (publish_and_check_last(v, 5, partials, &ctrl->counter[CS_MID], &sflag)) {
+  for (int m = 0; m < 5; ++m) v[m] = acc[m];
+  block_reduce<T, 5, false>(v, sred);
+  if (publish_and_check_last<T>(v, 5, reinterpret_cast<T*>(partials), &ctrl->counter[CS_MID], &sflag)) {
+    T tt[5];
+    gather_partials<T, 5, false>(tt, reinterpret_cast<const T*>(partials), sred);
     double tot[5];
-    gather_partials<5, false>(tot, partials, sred);
+    for (int m_ = 0; m_ < 5; ++m_) tot[m_] = (double)tt[m_];
     if (tid == 0) {
       const double w = kp.hd * kp.inv_ntot;
       ctrl->rd = tot[0] * w;
@@ -277,27 +299,43 @@ __global__ void k_spec6_combine(T* a, const T* b, KParams kp, const T* sx, const
   }
 }
 
+__global__ void k_widen_f64(double* out, const float* in, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
 template <typename T>
-__global__ void k_spec_apply_T(T* a, KParams kp, const T* sx, const T* sy, const T* sz, size_t n) {
+__global__ void k_spec_apply_T(T* a, T scale, KParams kp, const T* sx, const T* sy, const T* sz, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const T mu = mu_at(i, kp, sx, sy, sz);
-    a[i] = (mu > T(0)) ? a[i] / mu : T(0);
+    a[i] = (mu > T(0)) ? scale * a[i] / mu : T(0);
   }
 }
 
 // ------------------------------------------------------------ launch helpers
-template <typename T, int N>
+// Radix of the register passes: 16 for the FP32 row/column passes; 8 where
+// radix 16's register footprint would halve the occupancy (FP64, and the
+// middle pass, which also holds the symbol-division state).
+template <typename T>
+constexpr int radix_pass() {
+  return sizeof(T) == 8 ? 8 : 16;
+}
+template <typename T>
+constexpr int radix_mid() {
+  return 8;
+}
+template <typename T, int N, int RM, bool ROWS>
 size_t pair_smem() {
-  return 2 * (size_t)(N + PAD) * sizeof(T);
+  return 2 * (size_t)line_stride_words<LineFFT<T, N, RM>::L, ROWS>() * sizeof(T);
 }
 
 // Number of column pairs per block: fill 256 threads, bounded by the shared
 // memory budget and by the available pairs; a power of two.
-template <typename T, int N>
+template <typename T, int N, int RM, bool ROWS>
 int pick_pairs(int avail_pairs) {
-  using F = LineFFT<T, N>;
+  using F = LineFFT<T, N, RM>;
   int pairs = kThreads / F::TS;
-  while (pairs > 1 && (size_t)pairs * pair_smem<T, N>() > kMaxSmem) pairs >>= 1;
+  while (pairs > 1 && (size_t)pairs * pair_smem<T, N, RM, ROWS>() > kMaxSmem) pairs >>= 1;
   while (pairs > 1 && pairs > avail_pairs) pairs >>= 1;
   return pairs < 1 ? 1 : pairs;
 }
@@ -305,32 +343,35 @@ int pick_pairs(int avail_pairs) {
 template <typename T, int N>
 cudaError_t rows_impl(const T* src, T* dst, int nrows, T scale, const int* done, const T* twc,
                       const T* tws, cudaStream_t st) {
-  using F = LineFFT<T, N>;
-  const int pairs = pick_pairs<T, N>(1 << 30);
+  constexpr int RM = radix_pass<T>();
+  using F = LineFFT<T, N, RM>;
+  const int pairs = pick_pairs<T, N, RM, true>(1 << 30);
   const int rows_per_block = 2 * pairs;
   const int grid = (nrows + rows_per_block - 1) / rows_per_block;
-  k_dht_rows<T, N><<<grid, pairs * F::TS, pairs * pair_smem<T, N>(), st>>>(src, dst, nrows, scale, done,
-                                                                           twc, tws);
+  k_dht_rows<T, N, RM><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, true>(), st>>>(src, dst, nrows, scale, done,
+                                                                               twc, tws);
   return cudaGetLastError();
 }
 
 template <typename T, int N>
 cudaError_t cols_impl(T* data, int nx, int nouter, size_t line_stride, size_t outer_stride, T scale,
                       const int* done, const T* twc, const T* tws, cudaStream_t st) {
-  using F = LineFFT<T, N>;
-  const int pairs = pick_pairs<T, N>(nx / 2);
+  constexpr int RM = radix_pass<T>();
+  using F = LineFFT<T, N, RM>;
+  const int pairs = pick_pairs<T, N, RM, false>(nx / 2);
   dim3 grid(nx / (2 * pairs), nouter);
-  k_dht_cols<T, N><<<grid, pairs * F::TS, pairs * pair_smem<T, N>(), st>>>(data, line_stride, outer_stride,
-                                                                           scale, done, twc, tws);
+  k_dht_cols<T, N, RM><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, false>(), st>>>(data, line_stride, outer_stride,
+                                                                               scale, done, twc, tws);
   return cudaGetLastError();
 }
 
 template <typename T, int N>
-cudaError_t mid_impl(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* zeta, T* dspec,
+cudaError_t mid_impl(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* xi, T* dspec,
                      const AxisTables<T>& tb, cudaStream_t st) {
-  using F = LineFFT<T, N>;
+  constexpr int RM = radix_mid<T>();
+  using F = LineFFT<T, N, RM>;
   const int nx = kp.nx;
-  const int pairs = pick_pairs<T, N>(nx / 2);
+  const int pairs = pick_pairs<T, N, RM, false>(nx / 2);
   size_t line_stride, outer_stride;
   int nouter;
   const T* symo;
@@ -355,22 +396,23 @@ cudaError_t mid_impl(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T
     tws = tb.tws[2];
   }
   dim3 grid(nx / (2 * pairs), nouter);
-  const size_t sm = pairs * pair_smem<T, N>();
+  const size_t sm = pairs * pair_smem<T, N, RM, false>();
   if (kp.order == 4)
-    k_mid<T, N, 4><<<grid, pairs * F::TS, sm, st>>>(data, line_stride, outer_stride, kp, ctrl, partials,
-                                                   zeta, dspec, tb.sym[0], symo, syml, twc, tws);
+    k_mid<T, N, 4, RM><<<grid, pairs * F::TS, sm, st>>>(data, line_stride, outer_stride, kp, ctrl, partials,
+                                                   xi, dspec, tb.sym[0], symo, syml, twc, tws);
   else
-    k_mid<T, N, 6><<<grid, pairs * F::TS, sm, st>>>(data, line_stride, outer_stride, kp, ctrl, partials,
-                                                   zeta, dspec, tb.sym[0], symo, syml, twc, tws);
+    k_mid<T, N, 6, RM><<<grid, pairs * F::TS, sm, st>>>(data, line_stride, outer_stride, kp, ctrl, partials,
+                                                   xi, dspec, tb.sym[0], symo, syml, twc, tws);
   return cudaGetLastError();
 }
 
 template <typename T, int N>
 void set_attrs() {
-  cudaFuncSetAttribute(k_dht_rows<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_dht_cols<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_mid<T, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_mid<T, N, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  constexpr int RP = radix_pass<T>(), RD = radix_mid<T>();
+  cudaFuncSetAttribute(k_dht_rows<T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_cols<T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_mid<T, N, 4, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_mid<T, N, 6, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
 }
 
 #define PSD_DISPATCH_N(n, CALL)      \
@@ -414,10 +456,10 @@ cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const i
 }
 
 template <typename T>
-cudaError_t launch_mid(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* zeta, T* dspec,
+cudaError_t launch_mid(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* xi, T* dspec,
                        const AxisTables<T>& tb, cudaStream_t st) {
   const int n = kp.dim == 2 ? kp.ny : kp.nz;
-  PSD_DISPATCH_N(n, (mid_impl<T, NN>(data, kp, ctrl, partials, zeta, dspec, tb, st)));
+  PSD_DISPATCH_N(n, (mid_impl<T, NN>(data, kp, ctrl, partials, xi, dspec, tb, st)));
 }
 
 template <typename T>
@@ -430,10 +472,16 @@ cudaError_t launch_spec6_combine(T* a, const T* b, const KParams& kp, const Axis
 }
 
 template <typename T>
-cudaError_t launch_spec_apply_T(T* a, const KParams& kp, const AxisTables<T>& tb, cudaStream_t st) {
+cudaError_t launch_spec_apply_T(T* a, T scale, const KParams& kp, const AxisTables<T>& tb, cudaStream_t st) {
   const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
   const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
-  k_spec_apply_T<T><<<grid, 256, 0, st>>>(a, kp, tb.sym[0], tb.sym[1], tb.sym[2], n);
+  k_spec_apply_T<T><<<grid, 256, 0, st>>>(a, scale, kp, tb.sym[0], tb.sym[1], tb.sym[2], n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen_f64(double* out, const float* in, size_t n, cudaStream_t st) {
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+  k_widen_f64<<<grid, 256, 0, st>>>(out, in, n);
   return cudaGetLastError();
 }
 
@@ -465,7 +513,7 @@ void init_dht_attributes() {
                                      cudaStream_t);                                                    \
   template cudaError_t launch_spec6_combine<T>(T*, const T*, const KParams&, const AxisTables<T>&,      \
                                                cudaStream_t);                                          \
-  template cudaError_t launch_spec_apply_T<T>(T*, const KParams&, const AxisTables<T>&, cudaStream_t);
+  template cudaError_t launch_spec_apply_T<T>(T*, T, const KParams&, const AxisTables<T>&, cudaStream_t);
 PSD_INST(float)
 PSD_INST(double)
 

@@ -64,9 +64,32 @@ __device__ __forceinline__ void flux(const T (&g)[3], T beta, T (&out)[3]) {
   for (int c = 0; c < 3; ++c) out[c] = f * g[c];
 }
 
+// Linearised flux W(a) e = |a|^{p-2} e + (p-2)|a|^{p-4} (a.e) a (the second
+// variation of Sec. 5.3; the (p-2)-term is 0 where a = 0 for p < 4).
+template <int PK, typename T>
+__device__ __forceinline__ void flux_lin(const T (&a)[3], const T (&e)[3], T beta, T (&out)[3]) {
+  const T a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+  const T ae = a[0] * e[0] + a[1] * e[1] + a[2] * e[2];
+  if (PK == PK_4) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = a2 * e[c] + T(2) * ae * a[c];
+  } else {
+    const T f = pow(a2, beta);
+    const T w = (a2 > T(0)) ? T(2) * beta * pow(a2, beta - T(1)) * ae : T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = f * e[c] + w * a[c];
+  }
+}
+
 // Last-block bookkeeping of the residual kernel.
 __device__ void residual_epilogue(Ctrl* ctrl, const KParams& kp, double sum2, double maxabs, int norm,
-                                  int update_iter) {
+                                  int update_iter, bool hvp = false) {
+  if (hvp) {
+    ctrl->c1 = sum2 * kp.hd;
+    ctrl->c2 = maxabs;
+    ctrl->counter[CS_RES] = 0;
+    return;
+  }
   if (update_iter) {
     const int it = ctrl->iter;
     if (ctrl->hist_alpha != nullptr && it < ctrl->hist_cap) ctrl->hist_alpha[it] = ctrl->alpha;
@@ -98,12 +121,12 @@ __global__ void __launch_bounds__(NT)
     k_res3d(ResArgs<T> a, KParams kp, Ctrl* ctrl, double* partials, int zc) {
   if (ctrl->done) return;
   constexpr int SXM = BX + 4, SYM = BY3 + 4;
-  constexpr int NB = (MODE == RM_INNER) ? 2 : 1;
+  constexpr int NB = (MODE != RM_PLAIN) ? 2 : 1;
   __shared__ T su[5][SYM][SXM];
   __shared__ T sb[NB][SYM][SXM];
   __shared__ T sl[3][BY3 + 2][BX + 2];
   __shared__ T sf[2][3][BY3 + 1][BX + 1];
-  __shared__ double sred[32 * 2];
+  __shared__ T sred[32 * 2];
   __shared__ int sflag;
 
   const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
@@ -140,7 +163,7 @@ __global__ void __launch_bounds__(NT)
     }
   };
   auto load_base = [&](int zz) {
-    if (MODE != RM_INNER) return;
+    if (MODE == RM_PLAIN) return;
     const int sl_ = bslot(zz);
     const size_t gz = (size_t)wrapi(zz, nz) * plane;
     for (int idx = tid; idx < SX * SY; idx += NT) {
@@ -176,10 +199,13 @@ __global__ void __launch_bounds__(NT)
       const int vy = idx / VX, vx = idx - vy * VX;
       T g[3], F[3];
       grad8(su[c0], su[c1], vy, vx, g);
-      if (MODE == RM_INNER) {
+      if (MODE != RM_PLAIN) {
         T ab[3];
         grad8(sb[bslot(zz) % NB], sb[bslot(zz + 1) % NB], vy, vx, ab);
-        flux_diff<PK>(ab, g, beta, F);
+        if (MODE == RM_INNER)
+          flux_diff<PK>(ab, g, beta, F);
+        else
+          flux_lin<PK>(ab, g, beta, F);
       } else {
         flux<PK>(g, beta, F);
       }
@@ -210,11 +236,13 @@ __global__ void __launch_bounds__(NT)
       const size_t g = gz + (size_t)(y0 + ty) * nx + (x0 + tx);
       T r;
       if (MODE == RM_INNER)
-        r = a.f[g] - ((cu * uc + se2 * bih) - s * div);
+        r = (a.f ? a.f[g] : T(0)) - ((cu * uc + se2 * bih) - s * div);
+      else if (MODE == RM_HVP)
+        r = (cu * uc + se2 * bih) - s * div;
       else
-        r = a.f[g] - cu * uc + s * div - se2 * bih;
+        r = (a.f ? a.f[g] : T(0)) - cu * uc + s * div - se2 * bih;
       a.r[g] = r;
-      acc2 += r * r;
+      acc2 += (MODE == RM_HVP) ? uc * r : r * r;
       accm = fmax(accm, fabs(r));
     }
   };
@@ -237,12 +265,14 @@ __global__ void __launch_bounds__(NT)
     comp_out(z);
   }
 
-  double v[2] = {(double)acc2, (double)accm};
-  block_reduce<2, true>(v, sred);
-  if (publish_and_check_last(v, 2, partials, &ctrl->counter[CS_RES], &sflag)) {
+  T v[2] = {acc2, accm};
+  block_reduce<T, 2, true>(v, sred);
+  if (publish_and_check_last<T>(v, 2, reinterpret_cast<T*>(partials), &ctrl->counter[CS_RES], &sflag)) {
+    T tt[2];
+    gather_partials<T, 2, true>(tt, reinterpret_cast<const T*>(partials), sred);
     double tot[2];
-    gather_partials<2, true>(tot, partials, sred);
-    if (tid == 0) residual_epilogue(ctrl, kp, tot[0], tot[1], a.norm, a.update_iter);
+    for (int m_ = 0; m_ < 2; ++m_) tot[m_] = (double)tt[m_];
+    if (tid == 0) residual_epilogue(ctrl, kp, tot[0], tot[1], a.norm, a.update_iter, MODE == RM_HVP);
   }
 }
 
@@ -253,10 +283,10 @@ __global__ void __launch_bounds__(NT) k_res2d(ResArgs<T> a, KParams kp, Ctrl* ct
   constexpr int SXM = BX + 4, SYM = BY2 + 4;
   constexpr int NB = (MODE == RM_INNER) ? 1 : 1;
   __shared__ T su[SYM][SXM];
-  __shared__ T sb[(MODE == RM_INNER) ? SYM : 1][SXM];
+  __shared__ T sb[(MODE != RM_PLAIN) ? SYM : 1][SXM];
   __shared__ T sl[BY2 + 2][BX + 2];
   __shared__ T sf[2][BY2 + 1][BX + 1];
-  __shared__ double sred[32 * 2];
+  __shared__ T sred[32 * 2];
   __shared__ int sflag;
   (void)NB;
 
@@ -281,7 +311,7 @@ __global__ void __launch_bounds__(NT) k_res2d(ResArgs<T> a, KParams kp, Ctrl* ct
       if (lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2) a.u_out[g] = v;
     }
     su[ly][lx] = v;
-    if (MODE == RM_INNER) sb[ly][lx] = a.ubase[g];
+    if (MODE != RM_PLAIN) sb[ly][lx] = a.ubase[g];
   }
   __syncthreads();
   {
@@ -301,10 +331,13 @@ __global__ void __launch_bounds__(NT) k_res2d(ResArgs<T> a, KParams kp, Ctrl* ct
         g[1] = q2 * ((u10 - u00) + (u11 - u01));
         g[2] = T(0);
       }
-      if (MODE == RM_INNER) {
+      if (MODE != RM_PLAIN) {
         const T u00 = sb[vy + 1][vx + 1], u01 = sb[vy + 1][vx + 2], u10 = sb[vy + 2][vx + 1], u11 = sb[vy + 2][vx + 2];
         T ab[3] = {q2 * ((u01 - u00) + (u11 - u10)), q2 * ((u10 - u00) + (u11 - u01)), T(0)};
-        flux_diff<PK>(ab, g, beta, F);
+        if (MODE == RM_INNER)
+          flux_diff<PK>(ab, g, beta, F);
+        else
+          flux_lin<PK>(ab, g, beta, F);
       } else {
         flux<PK>(g, beta, F);
       }
@@ -324,19 +357,23 @@ __global__ void __launch_bounds__(NT) k_res2d(ResArgs<T> a, KParams kp, Ctrl* ct
     const size_t g = (size_t)(y0 + ty) * nx + (x0 + tx);
     T r;
     if (MODE == RM_INNER)
-      r = a.f[g] - ((cu * uc + se2 * bih) - s * div);
+      r = (a.f ? a.f[g] : T(0)) - ((cu * uc + se2 * bih) - s * div);
+    else if (MODE == RM_HVP)
+      r = (cu * uc + se2 * bih) - s * div;
     else
-      r = a.f[g] - cu * uc + s * div - se2 * bih;
+      r = (a.f ? a.f[g] : T(0)) - cu * uc + s * div - se2 * bih;
     a.r[g] = r;
-    acc2 += r * r;
+    acc2 += (MODE == RM_HVP) ? uc * r : r * r;
     accm = fmax(accm, fabs(r));
   }
-  double v[2] = {(double)acc2, (double)accm};
-  block_reduce<2, true>(v, sred);
-  if (publish_and_check_last(v, 2, partials, &ctrl->counter[CS_RES], &sflag)) {
+  T v[2] = {acc2, accm};
+  block_reduce<T, 2, true>(v, sred);
+  if (publish_and_check_last<T>(v, 2, reinterpret_cast<T*>(partials), &ctrl->counter[CS_RES], &sflag)) {
+    T tt[2];
+    gather_partials<T, 2, true>(tt, reinterpret_cast<const T*>(partials), sred);
     double tot[2];
-    gather_partials<2, true>(tot, partials, sred);
-    if (tid == 0) residual_epilogue(ctrl, kp, tot[0], tot[1], a.norm, a.update_iter);
+    for (int m_ = 0; m_ < 2; ++m_) tot[m_] = (double)tt[m_];
+    if (tid == 0) residual_epilogue(ctrl, kp, tot[0], tot[1], a.norm, a.update_iter, MODE == RM_HVP);
   }
 }
 
@@ -418,7 +455,8 @@ __device__ void linesearch_epilogue(Ctrl* ctrl, const KParams& kp, const double 
   const double lin = kp.cu * ctrl->dd + ctrl->tdd + kp.s * kp.eps2 * ctrl->lapdd;
   if (PK == PK_4) {
     int st = 0;
-    const double c1 = kp.s * kp.hd * tot[0], c2 = 3.0 * kp.s * kp.hd * tot[1], c3 = kp.s * kp.hd * tot[2];
+    // the kernels sum unscaled vertex gradients G = g / q: s g^4-terms = cdiv G^4-terms
+    const double c1 = kp.cdiv * kp.hd * tot[0], c2 = 3.0 * kp.cdiv * kp.hd * tot[1], c3 = kp.cdiv * kp.hd * tot[2];
     const double al = solve_cubic_alpha(ctrl->rd, lin, c1, c2, c3, &st);
     ctrl->c1 = c1;
     ctrl->c2 = c2;
@@ -431,8 +469,8 @@ __device__ void linesearch_epilogue(Ctrl* ctrl, const KParams& kp, const double 
   } else {
     // one safeguarded Newton step per launch; state in c1 (lo), c2 (hi), c3 (done flag)
     const double trial = ctrl->alpha;
-    const double qv = -ctrl->rd + trial * lin + kp.s * kp.hd * tot[0];
-    const double dqv = lin + kp.s * kp.hd * tot[1];
+    const double qv = -ctrl->rd + trial * lin + kp.cdiv * kp.hd * tot[0];
+    const double dqv = lin + kp.cdiv * kp.hd * tot[1];
     double lo = ctrl->c1, hi = ctrl->c2;
     if (qv < 0.0)
       lo = trial;
@@ -463,6 +501,12 @@ __device__ void linesearch_epilogue(Ctrl* ctrl, const KParams& kp, const double 
   ctrl->counter[CS_LS] = 0;
 }
 
+}  // namespace
+}  // namespace psd
+#include "stencil3d_col.cuh"
+namespace psd {
+namespace {
+
 template <typename T, int PK, bool INNER>
 __global__ void __launch_bounds__(NT)
     k_ls3d(const T* __restrict__ u, const T* __restrict__ ubase, const T* __restrict__ d, KParams kp, Ctrl* ctrl,
@@ -472,7 +516,7 @@ __global__ void __launch_bounds__(NT)
   constexpr int SXM = BX + 1, SYM = BY3 + 1;
   __shared__ T su[2][SYM][SXM];
   __shared__ T sd[2][SYM][SXM];
-  __shared__ double sred[32 * 3];
+  __shared__ T sred[32 * 3];
   __shared__ int sflag;
   const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
   const int TX = nx < BX ? nx : BX, TY = ny < BY3 ? ny : BY3;
@@ -480,7 +524,6 @@ __global__ void __launch_bounds__(NT)
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
   const size_t plane = (size_t)nx * ny;
-  const T q4 = T(0.25) * (T)kp.inv_h;
   const T beta = (T)(0.5 * (kp.p - 2.0)), pm2 = (T)(kp.p - 2.0);
   const T trial = (PK == PK_4) ? T(0) : (T)ctrl->alpha;
   auto load = [&](int zz) {
@@ -498,9 +541,9 @@ __global__ void __launch_bounds__(NT)
   auto grad = [&](T (&f0)[SYM][SXM], T (&f1)[SYM][SXM], int vy, int vx, T (&g)[3]) {
     const T u000 = f0[vy][vx], u001 = f0[vy][vx + 1], u010 = f0[vy + 1][vx], u011 = f0[vy + 1][vx + 1];
     const T u100 = f1[vy][vx], u101 = f1[vy][vx + 1], u110 = f1[vy + 1][vx], u111 = f1[vy + 1][vx + 1];
-    g[0] = q4 * (((u001 - u000) + (u011 - u010)) + ((u101 - u100) + (u111 - u110)));
-    g[1] = q4 * (((u010 - u000) + (u011 - u001)) + ((u110 - u100) + (u111 - u101)));
-    g[2] = q4 * (((u100 - u000) + (u101 - u001)) + ((u110 - u010) + (u111 - u011)));
+    g[0] = ((u001 - u000) + (u011 - u010)) + ((u101 - u100) + (u111 - u110));
+    g[1] = ((u010 - u000) + (u011 - u001)) + ((u110 - u100) + (u111 - u101));
+    g[2] = ((u100 - u000) + (u101 - u001)) + ((u110 - u010) + (u111 - u011));
   };
   T acc[3] = {T(0), T(0), T(0)};
   load(z0);
@@ -517,11 +560,13 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
   }
-  double v[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-  block_reduce<3, false>(v, sred);
-  if (publish_and_check_last(v, 3, partials, &ctrl->counter[CS_LS], &sflag)) {
+  T v[3] = {acc[0], acc[1], acc[2]};
+  block_reduce<T, 3, false>(v, sred);
+  if (publish_and_check_last<T>(v, 3, reinterpret_cast<T*>(partials), &ctrl->counter[CS_LS], &sflag)) {
+    T tt[3];
+    gather_partials<T, 3, false>(tt, reinterpret_cast<const T*>(partials), sred);
     double tot[3];
-    gather_partials<3, false>(tot, partials, sred);
+    for (int m_ = 0; m_ < 3; ++m_) tot[m_] = (double)tt[m_];
     if (tid == 0) linesearch_epilogue<PK>(ctrl, kp, tot);
   }
 }
@@ -535,14 +580,13 @@ __global__ void __launch_bounds__(NT)
   constexpr int SXM = BX + 1, SYM = BY2 + 1;
   __shared__ T su[SYM][SXM];
   __shared__ T sd[SYM][SXM];
-  __shared__ double sred[32 * 3];
+  __shared__ T sred[32 * 3];
   __shared__ int sflag;
   const int nx = kp.nx, ny = kp.ny;
   const int TX = nx < BX ? nx : BX, TY = ny < BY2 ? ny : BY2;
   const int SX = TX + 1, SY = TY + 1;
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const T q2 = T(0.5) * (T)kp.inv_h;
   const T beta = (T)(0.5 * (kp.p - 2.0)), pm2 = (T)(kp.p - 2.0);
   const T trial = (PK == PK_4) ? T(0) : (T)ctrl->alpha;
   for (int idx = tid; idx < SX * SY; idx += NT) {
@@ -557,17 +601,19 @@ __global__ void __launch_bounds__(NT)
   T acc[3] = {T(0), T(0), T(0)};
   for (int idx = tid; idx < TX * TY; idx += NT) {
     const int vy = idx / TX, vx = idx - vy * TX;
-    T av[3] = {q2 * ((su[vy][vx + 1] - su[vy][vx]) + (su[vy + 1][vx + 1] - su[vy + 1][vx])),
-               q2 * ((su[vy + 1][vx] - su[vy][vx]) + (su[vy + 1][vx + 1] - su[vy][vx + 1])), T(0)};
-    T bv[3] = {q2 * ((sd[vy][vx + 1] - sd[vy][vx]) + (sd[vy + 1][vx + 1] - sd[vy + 1][vx])),
-               q2 * ((sd[vy + 1][vx] - sd[vy][vx]) + (sd[vy + 1][vx + 1] - sd[vy][vx + 1])), T(0)};
+    T av[3] = {(su[vy][vx + 1] - su[vy][vx]) + (su[vy + 1][vx + 1] - su[vy + 1][vx]),
+               (su[vy + 1][vx] - su[vy][vx]) + (su[vy + 1][vx + 1] - su[vy][vx + 1]), T(0)};
+    T bv[3] = {(sd[vy][vx + 1] - sd[vy][vx]) + (sd[vy + 1][vx + 1] - sd[vy + 1][vx]),
+               (sd[vy + 1][vx] - sd[vy][vx]) + (sd[vy + 1][vx + 1] - sd[vy][vx + 1]), T(0)};
     ls_accumulate<PK>(av, bv, trial, beta, pm2, acc);
   }
-  double v[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-  block_reduce<3, false>(v, sred);
-  if (publish_and_check_last(v, 3, partials, &ctrl->counter[CS_LS], &sflag)) {
+  T v[3] = {acc[0], acc[1], acc[2]};
+  block_reduce<T, 3, false>(v, sred);
+  if (publish_and_check_last<T>(v, 3, reinterpret_cast<T*>(partials), &ctrl->counter[CS_LS], &sflag)) {
+    T tt[3];
+    gather_partials<T, 3, false>(tt, reinterpret_cast<const T*>(partials), sred);
     double tot[3];
-    gather_partials<3, false>(tot, partials, sred);
+    for (int m_ = 0; m_ < 3; ++m_) tot[m_] = (double)tt[m_];
     if (tid == 0) linesearch_epilogue<PK>(ctrl, kp, tot);
   }
 }
@@ -593,10 +639,12 @@ __global__ void __launch_bounds__(NT) k_norms(const double* x, size_t n, double 
     v[1] += t * t;
     v[2] = fmax(v[2], fabs(t));
   }
-  block_reduce<3, true>(v, sred);
-  if (publish_and_check_last(v, 3, partials, &c->counter[CS_MISC], &sflag)) {
+  block_reduce<double, 3, true>(v, sred);
+  if (publish_and_check_last<double>(v, 3, partials, &c->counter[CS_MISC], &sflag)) {
+    double tt[3];
+    gather_partials<double, 3, true>(tt, partials, sred);
     double tot[3];
-    gather_partials<3, true>(tot, partials, sred);
+    for (int m_ = 0; m_ < 3; ++m_) tot[m_] = (double)tt[m_];
     if (threadIdx.x == 0) {
       c->rd = tot[0];
       c->res_l2 = sqrt(hd * tot[1]);
@@ -617,6 +665,25 @@ __global__ void k_accumulate_f64(double* u, const float* delta, float* u32, size
   }
 }
 
+// sum x (y + z) (z may be null) -> c->rd
+__global__ void __launch_bounds__(NT) k_dot(const double* x, const double* y, const double* z, size_t n, Ctrl* c,
+                                            double* partials) {
+  __shared__ double sred[32];
+  __shared__ int sflag;
+  double v[1] = {0.0};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    v[0] += x[i] * (z ? y[i] + z[i] : y[i]);
+  block_reduce<double, 1, false>(v, sred);
+  if (publish_and_check_last<double>(v, 1, partials, &c->counter[CS_MISC], &sflag)) {
+    double tt[1];
+    gather_partials<double, 1, false>(tt, partials, sred);
+    if (threadIdx.x == 0) {
+      c->rd = tt[0];
+      c->counter[CS_MISC] = 0;
+    }
+  }
+}
+
 inline int grid1d(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
 
 int pick_zc(int nz, int nblk_xy) {
@@ -633,7 +700,10 @@ cudaError_t res_impl(const ResArgs<T>& a, const KParams& kp, Ctrl* ctrl, double*
     const int gx = kp.nx / TX, gy = kp.ny / TY;
     const int zc = pick_zc(kp.nz, gx * gy);
     dim3 grid(gx, gy, kp.nz / zc);
-    k_res3d<T, PK, MODE><<<grid, NT, 0, st>>>(a, kp, ctrl, partials, zc);
+    if (kp.nx >= 32 && kp.ny >= 8)
+      k_res3d_col<T, PK, MODE><<<grid, NT, 0, st>>>(a, kp, ctrl, partials, zc);
+    else
+      k_res3d<T, PK, MODE><<<grid, NT, 0, st>>>(a, kp, ctrl, partials, zc);
   } else {
     const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY2 ? kp.ny : BY2;
     dim3 grid(kp.nx / TX, kp.ny / TY);
@@ -650,7 +720,10 @@ cudaError_t ls_impl(const T* u, const T* ubase, const T* d, const KParams& kp, C
     const int gx = kp.nx / TX, gy = kp.ny / TY;
     const int zc = pick_zc(kp.nz, gx * gy);
     dim3 grid(gx, gy, kp.nz / zc);
-    k_ls3d<T, PK, INNER><<<grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, zc);
+    if (kp.nx >= 32 && kp.ny >= 8)
+      k_ls3d_col<T, PK, INNER><<<grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, zc);
+    else
+      k_ls3d<T, PK, INNER><<<grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, zc);
   } else {
     const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY2 ? kp.ny : BY2;
     dim3 grid(kp.nx / TX, kp.ny / TY);
@@ -667,6 +740,10 @@ cudaError_t launch_residual(const ResArgs<T>& a, int mode, int pk, const KParams
   if (mode == RM_INNER) {
     if (pk == PK_4) return res_impl<T, PK_4, RM_INNER>(a, kp, ctrl, partials, st);
     return res_impl<T, PK_GEN, RM_INNER>(a, kp, ctrl, partials, st);
+  }
+  if (mode == RM_HVP) {
+    if (pk == PK_4) return res_impl<T, PK_4, RM_HVP>(a, kp, ctrl, partials, st);
+    return res_impl<T, PK_GEN, RM_HVP>(a, kp, ctrl, partials, st);
   }
   if (pk == PK_4) return res_impl<T, PK_4, RM_PLAIN>(a, kp, ctrl, partials, st);
   return res_impl<T, PK_GEN, RM_PLAIN>(a, kp, ctrl, partials, st);
@@ -697,6 +774,11 @@ cudaError_t launch_linesearch(const T* u, const T* ubase, const T* d, int pk, co
 template <typename T>
 cudaError_t launch_axpby(T* y, const T* x, const T* z, double a, double b, double c, size_t n, cudaStream_t st) {
   k_axpby<T><<<grid1d(n), 256, 0, st>>>(y, x, z, a, b, c, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_dot(const double* x, const double* y, const double* z, size_t n, Ctrl* c, double* partials,
+                       cudaStream_t st) {
+  k_dot<<<std::min(grid1d(n), 1024), NT, 0, st>>>(x, y, z, n, c, partials);
   return cudaGetLastError();
 }
 cudaError_t launch_norms(const double* x, size_t n, double hd, Ctrl* c, double* partials, cudaStream_t st) {

@@ -29,32 +29,39 @@ cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const i
 
 // The middle pass along the slowest axis (y in 2D, z in 3D) of the
 // preconditioner: forward DHT, division by the symbol of L_h, Parseval sums
-// into ctrl, inverse DHT (with the 1/N of the whole transform).  Order 6 also
-// advances zeta += alpha * dspec, subtracts zeta/mu (the T_h[u - g] term),
-// stores the new direction spectrum in dspec and decides convergence on the
+// into ctrl, inverse DHT (with the 1/N of the whole transform).  Order 6
+// also advances xi -= alpha_prev dspec / mu (xi: the transformed linear part
+// of the residual not formed by the stencil kernel, -T_h[u - g] or
+// R_outer - T_h[delta]), adds it to the transformed local residual, stores
+// the new direction spectrum in dspec and decides convergence on the
 // spectral residual norm.
 template <typename T>
-cudaError_t launch_mid(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* zeta, T* dspec,
+cudaError_t launch_mid(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* xi, T* dspec,
                        const AxisTables<T>& tb, cudaStream_t st);
+// out = (double) in, elementwise.
+cudaError_t launch_widen_f64(double* out, const float* in, size_t n, cudaStream_t st);
 
 // Spectral helpers (order 6, off the hot loop).
 // spec6_combine: a <- (mu == 0) ? 0 : a - b / mu   (a, b full DHT spectra)
-// spec_apply_T:  a <- (mu == 0) ? 0 : a / mu
+// spec_apply_T:  a <- (mu == 0) ? 0 : scale * a / mu
 template <typename T>
 cudaError_t launch_spec6_combine(T* a, const T* b, const KParams& kp, const AxisTables<T>& tb,
                                  cudaStream_t st);
 template <typename T>
-cudaError_t launch_spec_apply_T(T* a, const KParams& kp, const AxisTables<T>& tb, cudaStream_t st);
+cudaError_t launch_spec_apply_T(T* a, T scale, const KParams& kp, const AxisTables<T>& tb, cudaStream_t st);
 
 // ------------------------------------------------------------------ stencils
-enum ResMode { RM_PLAIN = 0, RM_INNER = 1 };
+// RM_PLAIN: r = f - N_h^{loc}[u];  RM_INNER: r = R - (N_h^{loc}[ubase + delta]
+// - N_h^{loc}[ubase]);  RM_HVP: r = H v (H = dN_h/du at ubase, v = u_in),
+// with h^d sum v.(H v) into ctrl->c1 and max|H v| into ctrl->c2.
+enum ResMode { RM_PLAIN = 0, RM_INNER = 1, RM_HVP = 2 };
 
 template <typename T>
 struct ResArgs {
   const T* u_in;   // plain: iterate u; inner: correction delta
   const T* d;      // direction applied before evaluation (null: none)
   T* u_out;        // receives u_in + alpha d (only when d != null)
-  const T* f;      // plain: right-hand side f; inner: outer residual R
+  const T* f;      // plain: right-hand side f; inner: outer residual R (null: 0)
   const T* ubase;  // inner: the outer iterate (rounded); else null
   T* r;            // residual (order 6: local part, without T_h)
   int norm;        // 1: reduce ||r|| into ctrl and decide convergence
@@ -83,6 +90,9 @@ long long residual_grid_blocks(const KParams& kp);
 // y = a * x + b * z + c elementwise (x or z may be null = 0; may alias y).
 template <typename T>
 cudaError_t launch_axpby(T* y, const T* x, const T* z, double a, double b, double c, size_t n, cudaStream_t st);
+// sum x (y + z) -> c->rd (z may be null).
+cudaError_t launch_dot(const double* x, const double* y, const double* z, size_t n, Ctrl* c, double* partials,
+                       cudaStream_t st);
 // sum x -> c->rd, sqrt(hd sum x^2) -> c->res_l2, max|x| -> c->res_linf.
 cudaError_t launch_norms(const double* x, size_t n, double hd, Ctrl* c, double* partials, cudaStream_t st);
 // out = (float) in;  u += delta, u32 = (float) u  (mixed precision bookkeeping)

@@ -57,8 +57,8 @@ struct psd_context {
   double* ub = nullptr;     // second iterate buffer (ping-pong with the caller's u)
   double* W = nullptr;      // residual / transform work array
   double* D = nullptr;      // search direction
-  double* Z = nullptr;      // order 6: DHT spectrum of u - g
-  double* Dsp = nullptr;    // order 6: DHT spectrum of the direction
+  double* Z = nullptr;      // order 6: plain solve: xi = -DHT(u - g)/mu; mixed: DHT(u - g)
+  double* Dsp = nullptr;    // order 6: DHT spectrum of the last direction
   // FP32 work arrays (mixed)
   float* u32 = nullptr;
   float* da = nullptr;
@@ -66,7 +66,6 @@ struct psd_context {
   float* W32 = nullptr;
   float* D32 = nullptr;
   float* R32 = nullptr;
-  float* Z32 = nullptr;
   float* Dsp32 = nullptr;
 
   double* partials = nullptr;
@@ -285,13 +284,13 @@ psd_status full_dht(psd_context* c, T* x, T scale, const AxisTables<T>& tb) {
 
 // The search-direction solve L_h d = W of one PSD iteration (W is consumed).
 template <typename T>
-psd_status precond_passes(psd_context* c, T* W, T* D, Ctrl* ctrl, T* zeta, T* dspec, const AxisTables<T>& tb) {
+psd_status precond_passes(psd_context* c, T* W, T* D, Ctrl* ctrl, T* xi, T* dspec, const AxisTables<T>& tb) {
   const KParams& kp = c->kp;
   const int* done = &ctrl->done;
   const int nrows = kp.ny * kp.nz;
   { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_ROWS_FP64)); CK(psd::launch_dht_rows<T>(W, W, kp.nx, nrows, T(1), done, tb, c->st)); }
   if (kp.dim == 3) { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_COLS_FP64)); CK(psd::launch_dht_cols<T>(W, kp, 1, T(1), done, tb, c->st)); }
-  { ProfScope p_(c, cls_of<T>(PSD_PROF_MID_FP64)); CK(psd::launch_mid<T>(W, kp, ctrl, c->partials, zeta, dspec, tb, c->st)); }
+  { ProfScope p_(c, cls_of<T>(PSD_PROF_MID_FP64)); CK(psd::launch_mid<T>(W, kp, ctrl, c->partials, xi, dspec, tb, c->st)); }
   if (kp.dim == 3) { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_COLS_FP64)); CK(psd::launch_dht_cols<T>(W, kp, 1, T(1), done, tb, c->st)); }
   { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_ROWS_FP64)); CK(psd::launch_dht_rows<T>(W, D, kp.nx, nrows, T(1), done, tb, c->st)); }
   return PSD_OK;
@@ -325,10 +324,7 @@ psd_status ensure_fp32(psd_context* c) {
   TRY(alloc(c, &c->W32, c->N));
   TRY(alloc(c, &c->D32, c->N));
   TRY(alloc(c, &c->R32, c->N));
-  if (c->prm.order == 6) {
-    TRY(alloc(c, &c->Z32, c->N));
-    TRY(alloc(c, &c->Dsp32, c->N));
-  }
+  if (c->prm.order == 6) TRY(alloc(c, &c->Dsp32, c->N));
   return PSD_OK;
 }
 
@@ -353,6 +349,25 @@ psd_status residual64(psd_context* c, const double* u, const double* f, const do
   return PSD_OK;
 }
 
+// Sixth-order outer residual in the transform domain (mixed precision):
+// W <- DHT(P0[f - N_h^{loc}[u]] - T_h[u - g]) using zeta64 = DHT(u - g) in Z;
+// ||R||_2 by Parseval into *res.
+psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f, double* res) {
+  const KParams& kp = c->kp;
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0};
+  { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
+  TRY(full_dht<double>(c, c->W, 1.0, c->tb64));
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec6_combine<double>(c->W, c->Z, kp, c->tb64, c->st)); }
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(c->W, c->N, kp.hd * kp.inv_ntot, c->ctrl2, c->partials, c->st)); }
+  Ctrl h2;
+  TRY(read_ctrl(c, c->ctrl2, h2));
+  *res = h2.res_l2;
+  return PSD_OK;
+}
+
 // Plain FP64 PSD.
 psd_status solve_fp64(psd_context* c, const double* f, const double* g, double* u, psd_info* info) {
   TRY(ensure_fp64(c));
@@ -367,9 +382,11 @@ psd_status solve_fp64(psd_context* c, const double* f, const double* g, double* 
   TRY(upload_ctrl(c, c->ctrl, h));
   CK(cudaEventRecord(c->ev0, c->st));
   if (kp.order == 6) {
+    // xi_0 = DHT(-T_h[u0 - g]) = -DHT(u0 - g) / mu; the direction spectrum starts at 0
     CK(cudaMemsetAsync(c->Dsp, 0, c->N * sizeof(double), c->st));
     { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
     TRY(full_dht<double>(c, c->Z, 1.0, c->tb64));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec_apply_T<double>(c->Z, -1.0, kp, c->tb64, c->st)); }
   }
   {
     ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, kp.order == 4 ? 1 : 0, 0};
@@ -428,6 +445,11 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
     gbar = hg.rd / (double)c->N;
   }
   { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
+  if (six) {
+    // zeta64 = DHT(u0 - g), advanced with DHT(delta) after every correction
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
+    TRY(full_dht<double>(c, c->Z, 1.0, c->tb64));
+  }
   int inner_total = 0, outer = 0;
   int status = PSD_ERR_NOCONV;
   double res = NAN, resinf = -1, last_alpha = 0;
@@ -436,6 +458,10 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
     if (delta) {
       { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, delta, c->u32, c->N, c->st)); }
       if (six) {
+        // zeta64 += DHT(delta), in FP64
+        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_widen_f64(c->D, delta, c->N, c->st)); }
+        TRY(full_dht<double>(c, c->D, 1.0, c->tb64));
+        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, c->Z, c->D, 1.0, 1.0, 0.0, c->N, c->st)); }
         // keep mean(u) = mean(g) exactly: delta is mean-zero only up to FP32 rounding
         Ctrl hu;
         { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
@@ -445,13 +471,20 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
         { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
       }
     }
-    TRY(residual64(c, u, f, g, c->W));
+    if (six) {
+      // the outer residual stays in the transform domain; the inner solve adds
+      // it to its own transformed residual in the middle pass
+      TRY(outer_residual6_spec(c, u, f, &res));
+      resinf = -1.0;
+    } else {
+      TRY(residual64(c, u, f, g, c->W));
+      Ctrl h2;
+      TRY(read_ctrl(c, c->ctrl2, h2));
+      res = h2.res_l2;
+      resinf = h2.res_linf;
+    }
     ++outer;
     { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->R32, c->W, c->N, c->st)); }
-    Ctrl h2;
-    TRY(read_ctrl(c, c->ctrl2, h2));
-    res = h2.res_l2;
-    resinf = h2.res_linf;
     if (!std::isfinite(res)) {
       status = PSD_ERR_NONFINITE;
       break;
@@ -476,13 +509,13 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
     h.pre_stall_max = kInnerStall;
     TRY(upload_ctrl(c, c->ctrl, h));
     CK(cudaMemsetAsync(c->da, 0, c->N * sizeof(float), c->st));
-    if (six) {
-      CK(cudaMemsetAsync(c->Z32, 0, c->N * sizeof(float), c->st));
-      CK(cudaMemsetAsync(c->Dsp32, 0, c->N * sizeof(float), c->st));
-    }
+    if (six) CK(cudaMemsetAsync(c->Dsp32, 0, c->N * sizeof(float), c->st));
     const int norm = six ? 0 : 1;
+    // order 6: the outer residual enters in the middle pass as the initial xi
+    // (R32 holds its spectrum and is advanced in place by the inner solve)
+    const float* rphys = six ? nullptr : c->R32;
     {
-      ResArgs<float> a{c->da, nullptr, nullptr, c->R32, c->u32, c->W32, norm, 0};
+      ResArgs<float> a{c->da, nullptr, nullptr, rphys, c->u32, c->W32, norm, 0};
       { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_INNER, c->pk, kp, c->ctrl, c->partials, c->st)); }
     }
     int k = 0;
@@ -491,9 +524,9 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
       for (int i = 0; i < kChunk; ++i, ++k) {
         float* cur = (k % 2 == 0) ? c->da : c->db;
         float* nxt = (k % 2 == 0) ? c->db : c->da;
-        TRY(precond_passes<float>(c, c->W32, c->D32, c->ctrl, c->Z32, c->Dsp32, c->tb32));
+        TRY(precond_passes<float>(c, c->W32, c->D32, c->ctrl, six ? c->R32 : nullptr, c->Dsp32, c->tb32));
         TRY(linesearch<float>(c, cur, c->u32, c->D32, c->ctrl));
-        ResArgs<float> a{cur, c->D32, nxt, c->R32, c->u32, c->W32, norm, 1};
+        ResArgs<float> a{cur, c->D32, nxt, rphys, c->u32, c->W32, norm, 1};
         { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_INNER, c->pk, kp, c->ctrl, c->partials, c->st)); }
       }
       TRY(read_ctrl(c, c->ctrl, hc));
@@ -576,6 +609,7 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
   kp.hd = params->dim == 3 ? params->h * params->h * params->h : params->h * params->h;
   c->N = (size_t)kp.nx * kp.ny * kp.nz;
   kp.inv_ntot = 1.0 / (double)c->N;
+  psd::finish_kparams(kp);
   c->pk = (params->p == 4.0) ? psd::PK_4 : psd::PK_GEN;
   static bool attrs = false;
   if (!attrs) {
@@ -614,7 +648,7 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
 psd_status psd_destroy(psd_handle c) {
   if (!c) return PSD_OK;
   void* ptrs[] = {c->tables, c->ub, c->W, c->D, c->Z, c->Dsp, c->u32, c->da, c->db, c->W32, c->D32,
-                  c->R32, c->Z32, c->Dsp32, c->partials, c->ctrl, c->ctrl2, c->d_hist};
+                  c->R32, c->Dsp32, c->partials, c->ctrl, c->ctrl2, c->d_hist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
@@ -736,6 +770,125 @@ psd_status psd_precond_solve(psd_handle c, const double* r, double* d) {
   return PSD_OK;
 }
 
+psd_status psd_hvp(psd_handle c, const double* u, const double* v, double* y, double* dot) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u || !v || !y) return fail(c, PSD_ERR_INVALID, "u, v and y are required");
+  if (c->prm.order != 4) return fail(c, PSD_ERR_UNSUPPORTED, "psd_hvp handles order 4");
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  ResArgs<double> a{v, nullptr, nullptr, nullptr, u, y, 0, 0};
+  { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_HVP, c->pk, c->kp, c->ctrl2, c->partials, c->st)); }
+  Ctrl o;
+  TRY(read_ctrl(c, c->ctrl2, o));
+  if (dot) *dot = o.c1;
+  return PSD_OK;
+}
+
+psd_status psd_adjoint(psd_handle c, const double* u, const double* grad_u, double* grad_f, double* grad_s,
+                       double tol_rel, int max_iter, psd_info* info) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u || !grad_u || !grad_f) return fail(c, PSD_ERR_INVALID, "u, grad_u and grad_f are required");
+  if (c->prm.order != 4) return fail(c, PSD_ERR_UNSUPPORTED, "psd_adjoint handles order 4");
+  if (max_iter < 1) return fail(c, PSD_ERR_INVALID, "max_iter must be >= 1");
+  if (!(tol_rel > 0)) tol_rel = 1e-12;
+  TRY(ensure_fp64(c));
+  TRY(alloc(c, &c->Z, c->N));
+  TRY(alloc(c, &c->Dsp, c->N));
+  const KParams& kp = c->kp;
+  const size_t bytes = c->N * sizeof(double);
+  // buffers: lam -> grad_f (copied at the end when grad_f aliases grad_u),
+  // r -> W, z -> D, p -> ub, Hp -> Z; Dsp: scratch of the middle pass
+  double* lam = (grad_f == grad_u) ? c->Dsp : grad_f;
+  double *r = c->W, *z = c->D, *pv = c->ub, *Hp = c->Z;
+  CK(cudaEventRecord(c->ev0, c->st));
+  CK(cudaMemsetAsync(lam, 0, bytes, c->st));
+  CK(cudaMemcpyAsync(r, grad_u, bytes, cudaMemcpyDeviceToDevice, c->st));
+  Ctrl h0;
+  init_ctrl(h0, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h0));
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(grad_u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+  Ctrl hb;
+  TRY(read_ctrl(c, c->ctrl2, hb));
+  const double bnorm = hb.res_l2;
+  int status = PSD_ERR_NOCONV, it = 0;
+  double rel = bnorm > 0 ? 1.0 : 0.0;
+  if (bnorm == 0.0) status = PSD_OK;
+  // z = L^{-1} r, (r, z) from the middle pass
+  auto precond = [&](double* rz) -> psd_status {
+    CK(cudaMemcpyAsync(z, r, bytes, cudaMemcpyDeviceToDevice, c->st));
+    Ctrl hp;
+    init_ctrl(hp, -1.0, 1 << 30);
+    TRY(upload_ctrl(c, c->ctrl2, hp));
+    TRY(precond_passes<double>(c, z, z, c->ctrl2, nullptr, nullptr, c->tb64));
+    Ctrl o;
+    TRY(read_ctrl(c, c->ctrl2, o));
+    *rz = o.rd;
+    return PSD_OK;
+  };
+  double rz = 0.0;
+  if (status != PSD_OK) {
+    TRY(precond(&rz));
+    CK(cudaMemcpyAsync(pv, z, bytes, cudaMemcpyDeviceToDevice, c->st));
+    for (it = 1; it <= max_iter; ++it) {
+      double pHp = 0.0;
+      TRY(psd_hvp(c, u, pv, Hp, &pHp));
+      if (!(pHp > 0.0) || !std::isfinite(pHp)) {
+        status = PSD_ERR_NONFINITE;
+        break;
+      }
+      const double al = rz / pHp;
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(lam, lam, pv, 1.0, al, 0.0, c->N, c->st)); }
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(r, r, Hp, 1.0, -al, 0.0, c->N, c->st)); }
+      Ctrl hn;
+      TRY(upload_ctrl(c, c->ctrl2, h0));
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(r, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+      TRY(read_ctrl(c, c->ctrl2, hn));
+      rel = hn.res_l2 / bnorm;
+      if (rel <= tol_rel) {
+        status = PSD_OK;
+        break;
+      }
+      double rz_new = 0.0;
+      TRY(precond(&rz_new));
+      const double be = rz_new / rz;
+      rz = rz_new;
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(pv, z, pv, 1.0, be, 0.0, c->N, c->st)); }
+    }
+    if (it > max_iter) it = max_iter;
+  }
+  // grad_s = -sum lam dN/ds, dN/ds = (N_h[u] - u)/s = (-r0 - u)/s with r0 = 0 - N_h[u]
+  double gs = 0.0;
+  {
+    Ctrl hz;
+    init_ctrl(hz, -1.0, 1 << 30);
+    TRY(upload_ctrl(c, c->ctrl2, hz));
+    ResArgs<double> a{u, nullptr, nullptr, nullptr, nullptr, c->W, 0, 0};
+    { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_dot(lam, c->W, u, c->N, c->ctrl2, c->partials, c->st)); }
+    Ctrl o;
+    TRY(read_ctrl(c, c->ctrl2, o));
+    gs = o.rd / kp.s;  // -sum lam (-W - u)/s
+  }
+  if (lam != grad_f) CK(cudaMemcpyAsync(grad_f, lam, bytes, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaEventRecord(c->ev1, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  if (grad_s) *grad_s = gs;
+  if (info) {
+    info->iters = it;
+    info->outer_iters = 0;
+    info->res_l2 = rel;
+    info->res_linf = -1.0;
+    info->last_alpha = 0.0;
+    info->wall_ms = ms;
+    info->status = status;
+  }
+  if (status != PSD_OK) fail(c, (psd_status)status, std::string("adjoint ended with ") + psd_status_string((psd_status)status));
+  return (psd_status)status;
+}
+
 psd_status psd_solve(psd_handle c, const double* f, const double* g, double* u, double* w, psd_info* info) {
   if (!c) return PSD_ERR_INVALID;
   if (!f || !u) return fail(c, PSD_ERR_INVALID, "f and u are required");
@@ -759,7 +912,7 @@ psd_status psd_solve(psd_handle c, const double* f, const double* g, double* u, 
     const double gbar = hg.rd / (double)c->N, fbar = hf.rd / (double)c->N;
     { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(w, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
     TRY(full_dht<double>(c, w, 1.0, c->tb64));
-    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec_apply_T<double>(w, kp, c->tb64, c->st)); }
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec_apply_T<double>(w, 1.0, kp, c->tb64, c->st)); }
     TRY(full_dht<double>(c, w, kp.inv_ntot, c->tb64));
     { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(w, w, nullptr, -1.0, 0.0, kp.s * kp.lam * gbar - fbar, c->N, c->st)); }
     CK(cudaStreamSynchronize(c->st));

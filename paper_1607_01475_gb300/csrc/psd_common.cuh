@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace psd {
 
 // Kinds of the vertex factor |g|^{p-2}: specialised p = 4 and a general p.
@@ -58,7 +60,20 @@ struct KParams {
   double inv_ntot;      // 1 / (nx ny nz)
   int order;
   int pad_;
+  // derived constants (set by finish_kparams): the column kernels work with
+  // unscaled vertex-gradient sums G = g / q and Laplacian sums h^2 Delta_h.
+  double q;             // 1 / (2^(d-1) h): g = q G
+  double cdiv;          // s q^p: s d.(|g|^{p-2} g) = cdiv * (sum of differences of |G|^{p-2} G)
+  double cbih;          // s eps^2 / h^4: s eps^2 Delta_h^2 u = cbih * (h^4 Delta_h^2 u)
 };
+
+// Fill the derived constants of KParams (host side).
+inline void finish_kparams(KParams& kp) {
+  kp.q = kp.inv_h / (kp.dim == 3 ? 4.0 : 2.0);
+  const double qp = (kp.p == 4.0) ? kp.q * kp.q * kp.q * kp.q : std::pow(kp.q, kp.p);
+  kp.cdiv = kp.s * qp;
+  kp.cbih = kp.s * kp.eps2 * kp.inv_h * kp.inv_h * kp.inv_h * kp.inv_h;
+}
 
 // ------------------------------------------------------------------ reductions
 
@@ -69,19 +84,21 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-__device__ __forceinline__ double warp_max(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
-// Reduce M doubles over the block (fixed order: warp butterflies, then warp
-// 0 over the warp results); the result is valid in thread 0.  The last value
-// is reduced with max when LASTMAX is set.  Requires blockDim to be a
-// multiple of 32 (<= 1024) or smaller than 32 (then thread 0 sums serially);
-// uses a shared scratch of 32*M doubles.
-template <int M, bool LASTMAX>
-__device__ __forceinline__ void block_reduce(double (&v)[M], double* sh) {
+// Reduce M values of type A over the block (fixed order: warp butterflies,
+// then warp 0 over the warp results); the result is valid in thread 0.  The
+// last value is reduced with max when LASTMAX is set.  FP32 kernels reduce
+// in float (GB300 issues FP64 at 1/64 of the FP32 rate), FP64 kernels in
+// double.  Requires blockDim to be a multiple of 32 (<= 1024) or smaller
+// than 32 (then thread 0 sums serially); uses a shared scratch of 32*M A's.
+template <typename A, int M, bool LASTMAX>
+__device__ __forceinline__ void block_reduce(A (&v)[M], A* sh) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
   if (nthr < 32) {
@@ -92,7 +109,7 @@ __device__ __forceinline__ void block_reduce(double (&v)[M], double* sh) {
     if (tid == 0) {
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        double acc = sh[m];
+        A acc = sh[m];
         for (int t = 1; t < nthr; ++t) acc = (LASTMAX && m == M - 1) ? fmax(acc, sh[t * M + m]) : acc + sh[t * M + m];
         v[m] = acc;
       }
@@ -112,7 +129,7 @@ __device__ __forceinline__ void block_reduce(double (&v)[M], double* sh) {
   if (wid == 0) {
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      double x = (lane < nw) ? sh[lane * M + m] : ((LASTMAX && m == M - 1) ? -1.0 : 0.0);
+      A x = (lane < nw) ? sh[lane * M + m] : ((LASTMAX && m == M - 1) ? A(-1) : A(0));
       v[m] = (LASTMAX && m == M - 1) ? warp_max(x) : warp_sum(x);
     }
   }
@@ -122,8 +139,9 @@ __device__ __forceinline__ void block_reduce(double (&v)[M], double* sh) {
 // Write this block's partials, then return true in every thread of the
 // block that finished last (threadFenceReduction pattern).  The last block
 // can then read all partials with __ldcg.
-__device__ __forceinline__ bool publish_and_check_last(const double* v, int M, double* partials,
-                                                       unsigned int* counter, int* sh_flag) {
+template <typename A>
+__device__ __forceinline__ bool publish_and_check_last(const A* v, int M, A* partials, unsigned int* counter,
+                                                       int* sh_flag) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
@@ -139,21 +157,21 @@ __device__ __forceinline__ bool publish_and_check_last(const double* v, int M, d
 
 // In the last block: sum the partials of all blocks in a fixed order (each
 // thread a strided subset, then the block tree), result in thread 0.
-template <int M, bool LASTMAX>
-__device__ __forceinline__ void gather_partials(double (&out)[M], const double* partials, double* sh) {
+template <typename A, int M, bool LASTMAX>
+__device__ __forceinline__ void gather_partials(A (&out)[M], const A* partials, A* sh) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
   const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
 #pragma unroll
-  for (int m = 0; m < M; ++m) out[m] = (LASTMAX && m == M - 1) ? -1.0 : 0.0;
+  for (int m = 0; m < M; ++m) out[m] = (LASTMAX && m == M - 1) ? A(-1) : A(0);
   for (unsigned int b = tid; b < nb; b += nthr) {
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      double x = __ldcg(partials + (size_t)b * M + m);
+      A x = __ldcg(partials + (size_t)b * M + m);
       out[m] = (LASTMAX && m == M - 1) ? fmax(out[m], x) : out[m] + x;
     }
   }
-  block_reduce<M, LASTMAX>(out, sh);
+  block_reduce<A, M, LASTMAX>(out, sh);
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {  // n a power of two

@@ -79,6 +79,7 @@ extern "C" psd_status psd_residual_noalloc(const psd_params* prm, const double* 
   kp.cu = 1.0;
   kp.hd = prm->dim == 3 ? prm->h * prm->h * prm->h : prm->h * prm->h;
   kp.inv_ntot = 1.0 / ((double)kp.nx * kp.ny * kp.nz);
+  psd::finish_kparams(kp);
   const long long blocks = psd::residual_grid_blocks(kp);
   if (blocks > kMaxBlocks) {
     char buf[160];
