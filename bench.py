@@ -112,8 +112,8 @@ def algorithmic_bytes_per_cell(cls, order):
         # inner (order 6): delta, d, ubase in; delta', r out.  FP64 plain: u, d, f in; u', r out
         "residual": (5 if order == 6 else 6) if fp32 else 5,
         "dht_rows": 2, "dht_cols": 2,
-        # order 6: W, zeta, dspec (+ the outer residual's spectrum in the inner solve) in; W, zeta, dspec out
-        "mid": (7 if fp32 else 6) if order == 6 else 2,
+        # order 6: the line W, xi and dspec each read and written once
+        "mid": 6 if order == 6 else 2,
         "linesearch": 3 if fp32 else 2,  # delta, ubase, d  /  u, d
     }
     base = cls.rsplit("_", 1)[0]

@@ -154,7 +154,8 @@ enum {
   PSD_PROF_MID_FP64 = 6,      PSD_PROF_MID_FP32 = 7,
   PSD_PROF_LINESEARCH_FP64 = 8, PSD_PROF_LINESEARCH_FP32 = 9,
   PSD_PROF_OTHER = 10,
-  PSD_PROF_CLASSES = 11
+  PSD_PROF_DHT_ROWS_FF = 11,  PSD_PROF_DHT_COLS_FF = 12,  /* float-float passes */
+  PSD_PROF_CLASSES = 13
 };
 
 /* Per-kernel timing (tracing).  While enabled, every kernel launch of this
@@ -198,6 +199,26 @@ psd_status psd_residual_noalloc(const psd_params* params, const double* u,
 
 /* Text of the last error of psd_residual_noalloc in this host thread.     */
 psd_status psd_noalloc_last_error(char* buf, size_t len);
+
+/* ---- Batches of independent instances (many uneven problem sizes). ----
+ * psd_batch_create makes one solver per parameter set (each with its own
+ * non-blocking stream; the stream fields of per_instance are ignored) and a
+ * pool of `workers` host threads (<= 0: min(count, 16)).  psd_batch_solve
+ * solves every instance i from the initial guess in u[i] (device arrays of
+ * instance i's size; g[i] for order-6 instances, g may be NULL when none is
+ * order 6) concurrently: the instances' kernels overlap on the GPU.  It
+ * synchronises the device before starting and returns when all instances
+ * are done; infos (host, count entries, may be NULL) receives per-instance
+ * statistics; the status is PSD_OK or the first failing instance's status
+ * (psd_batch_last_error names it).                                        */
+typedef struct psd_batch_ctx* psd_batch;
+psd_status psd_batch_create(const psd_params* per_instance, int count,
+                            int workers, psd_batch* out);
+psd_status psd_batch_solve(psd_batch b, const double* const* f,
+                           const double* const* g, double* const* u,
+                           psd_info* infos);
+psd_status psd_batch_destroy(psd_batch b);
+psd_status psd_batch_last_error(psd_batch b, char* buf, size_t len);
 
 /* Text of the last error on this handle (or of the last psd_create failure
  * when h is NULL), copied into buf (always NUL-terminated).                */

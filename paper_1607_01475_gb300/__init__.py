@@ -8,7 +8,7 @@ CPU fallback: if the library cannot be loaded, every call raises.
 """
 
 from ._lib import (  # noqa: F401
-    PSD_FP64, PSD_MIXED, PSDError, Solver, lib_path, load_library,
+    PSD_FP64, PSD_MIXED, Batch, PSDError, Solver, lib_path, load_library,
     psd_create, psd_destroy, psd_precond_solve, psd_residual, psd_residual_f32,
     psd_residual_noalloc, psd_hvp, psd_adjoint,
     psd_solve, psd_status_string,

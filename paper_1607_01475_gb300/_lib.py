@@ -13,6 +13,7 @@ _LIB_NAME = "libpsd.so"
 
 PSD_FP64 = 0
 PSD_MIXED = 1
+PSD_PROF_CLASSES = 13  # kernel classes of psd_profile_read
 
 _STATUS = {0: "PSD_OK", 1: "PSD_ERR_INVALID", 2: "PSD_ERR_NOMEM", 3: "PSD_ERR_CUDA",
            4: "PSD_ERR_NOCONV", 5: "PSD_ERR_TIMEOUT", 6: "PSD_ERR_UNSUPPORTED",
@@ -77,6 +78,12 @@ def load_library(build_if_missing=True):
     lib.psd_hvp.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.psd_adjoint.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int,
                                 ctypes.POINTER(PSDInfo)]
+    lib.psd_batch_create.argtypes = [ctypes.POINTER(PSDParams), ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+    lib.psd_batch_solve.argtypes = [H, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                    ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PSDInfo)]
+    lib.psd_batch_destroy.argtypes = [H]
+    lib.psd_batch_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
     lib.psd_residual_noalloc.argtypes = [ctypes.POINTER(PSDParams), D, D, D, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     lib.psd_noalloc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -85,7 +92,8 @@ def load_library(build_if_missing=True):
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
                  "psd_set_history", "psd_residual_f32", "psd_last_error", "psd_profile",
                  "psd_profile_read", "psd_residual_noalloc", "psd_noalloc_last_error", "psd_hvp",
-                 "psd_adjoint"):
+                 "psd_adjoint", "psd_batch_create", "psd_batch_solve", "psd_batch_destroy",
+                 "psd_batch_last_error"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -199,6 +207,57 @@ def psd_residual_noalloc(shape, h, p, s, eps, u, f, r, stream=None):
     return l2.value, linf.value
 
 
+def _params(order, shape, h, p, s, eps, lam=0.0, precision=PSD_FP64, tol=1e-10, max_iter=10000,
+            max_outer=20, stream=None):
+    dim = len(shape)
+    n = (shape[-1], shape[-2], shape[0] if dim == 3 else 1)
+    return PSDParams(order=order, dim=dim, n=(ctypes.c_int * 3)(*n), h=h, p=p, s=s, eps=eps, lam=lam,
+                     precision=precision, tol=tol, max_iter=max_iter, max_outer=max_outer, stream=stream)
+
+
+class Batch:
+    """Many independent instances solved concurrently (psd_batch_*).
+    ``instances``: list of dicts with keys order, shape, h, p, s, eps and
+    optionally lam, precision, tol, max_iter, max_outer."""
+
+    def __init__(self, instances, workers=0):
+        lib = load_library()
+        self.n = len(instances)
+        arr = (PSDParams * self.n)(*[_params(**inst) for inst in instances])
+        out = ctypes.c_void_p()
+        st = lib.psd_batch_create(arr, self.n, workers, ctypes.byref(out))
+        if st != 0:
+            buf = ctypes.create_string_buffer(512)
+            lib.psd_batch_last_error(None, buf, len(buf))
+            raise PSDError(st, buf.value.decode())
+        self.handle = out
+
+    def solve(self, fs, us, gs=None, allow_noconv=False):
+        lib = load_library()
+        P = ctypes.c_void_p * self.n
+        fp = P(*[_ptr(t).value for t in fs])
+        up = P(*[_ptr(t).value for t in us])
+        gp = P(*[(_ptr(t).value if t is not None else None) for t in gs]) if gs is not None else None
+        infos = (PSDInfo * self.n)()
+        st = lib.psd_batch_solve(self.handle, fp, gp, up, infos)
+        if st != 0 and not (allow_noconv and st == 4):
+            buf = ctypes.create_string_buffer(512)
+            lib.psd_batch_last_error(self.handle, buf, len(buf))
+            raise PSDError(st, buf.value.decode())
+        return [i.as_dict() for i in infos]
+
+    def close(self):
+        if self.handle:
+            load_library().psd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ------------------------------------------------------------- convenience
 
 class Solver:
@@ -261,7 +320,7 @@ class Solver:
     def profile_read(self, eff_us=8.0):
         """{class name: (ms, launches, effective ms, effective launches)}."""
         import numpy as np
-        n = 11
+        n = PSD_PROF_CLASSES
         ms = np.zeros(n)
         cnt = np.zeros(n, dtype=np.int64)
         ems = np.zeros(n)

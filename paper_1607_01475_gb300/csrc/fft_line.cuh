@@ -21,7 +21,28 @@
 
 #include <cuda_runtime.h>
 
+#include "ffloat.cuh"
+
 namespace psd {
+
+// Twiddle load through the read-only path, and x/2, for each element type.
+template <typename T>
+__device__ __forceinline__ T ld_tw(const T* p) {
+  return __ldg(p);
+}
+template <>
+__device__ __forceinline__ ff ld_tw<ff>(const ff* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return ff(v.x, v.y);
+}
+template <typename T>
+__device__ __forceinline__ T half_of(T x) {
+  return T(0.5) * x;
+}
+template <>
+__device__ __forceinline__ ff half_of<ff>(ff x) {
+  return ff_scale2(x, 0.5f);
+}
 
 // cos(2 pi m / 16), the 16th roots of unity (exact values of cos(pi/8),
 // sin(pi/8) and sqrt(2)/2).
@@ -123,7 +144,7 @@ struct LineFFT {
 #pragma unroll
         for (int r = 1; r < RP; ++r) {
           const int t = jm * r * (N / (NS * RP));
-          const T c = __ldg(twc + t), sn = __ldg(tws + t);
+          const T c = ld_tw(twc + t), sn = ld_tw(tws + t);
           const T a = xr[r], bb = xi[r];
           xr[r] = a * c + bb * sn;
           xi[r] = bb * c - a * sn;
@@ -171,8 +192,8 @@ __device__ __forceinline__ void dht_split(const T* sr, const T* si, int k, int N
   const int k2 = (N - k) & (N - 1);
   const int a = k + (k >> 4), b = k2 + (k2 >> 4);
   const T A = sr[a], B = si[a], C = sr[b], D = si[b];
-  h1 = T(0.5) * ((A - B) + (C + D));
-  h2 = T(0.5) * ((A + B) - (C - D));
+  h1 = half_of((A - B) + (C + D));
+  h2 = half_of((A + B) - (C - D));
 }
 
 }  // namespace psd

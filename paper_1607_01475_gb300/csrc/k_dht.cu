@@ -21,23 +21,55 @@ struct Vec2<double> {
   using type = double2;
 };
 
+// Storage <-> compute element conversions (FP32, FP64, or float-float on
+// FP64 storage).
+template <typename C, typename S>
+__device__ __forceinline__ C to_compute(S v) {
+  return C(v);
+}
+template <typename S, typename C>
+__device__ __forceinline__ S to_storage(C v) {
+  return S(v);
+}
+template <>
+__device__ __forceinline__ double to_storage<double, ff>(ff v) {
+  return ff_to_double(v);
+}
+
 constexpr int kThreads = 256;
 
-// Words between the real arrays of consecutive column pairs in shared memory
-// (each pair holds its real and imaginary line of F::L words).  Row passes
-// put two pairs in a warp and want the pair offset at 16 banks (stride = 8
-// mod 16); column passes put many pairs in a warp and want consecutive pairs
-// 2 banks apart (stride = 1 mod 16).
-template <int L, bool ROWS>
+// Elements between the real arrays of consecutive line pairs in shared
+// memory (each pair holds its real and imaginary line of F::L elements): the
+// smallest LS >= F::L with LS = r (mod M), chosen so that the accesses of a
+// warp in every pass of the line FFT spread over the 32 banks.  With EW the
+// element size in 4-byte words: row passes (a warp spans 32/TS pairs) want
+// r = m/2, M = m for m = TS/EW (odd LS when m < 2, free when m >= 32);
+// column passes (a warp spans `pairs` pairs, 32/pairs threads each) want
+// r = 16/k, M = 32/k for k = min(pairs EW, 16).  The rule was fitted to a
+// wavefront count of the access pattern of every pass over N = 16..1024.
+template <typename T, int N, int RM, bool ROWS>
 __host__ __device__ constexpr int line_stride_words() {
-  return ROWS ? L + ((8 - (L & 15)) & 15) : L + ((1 - (L & 15)) & 15);
+  constexpr int L = LineFFT<T, N, RM>::L, TS = LineFFT<T, N, RM>::TS, EW = (int)(sizeof(T) / 4);
+  int r = 0, M = 1;
+  if (ROWS) {
+    const int m = TS / EW;
+    if (m >= 32) return L;
+    r = m < 2 ? 1 : m / 2;
+    M = m < 2 ? 2 : m;
+  } else {
+    const int k = (kThreads / TS) * EW < 16 ? (kThreads / TS) * EW : 16;
+    r = 16 / k;
+    M = 32 / k;
+  }
+  return L + (((r - L) % M) + M) % M;
 }
 constexpr size_t kMaxSmem = 96 * 1024;
 
 // -------------------------------------------------------------- x (rows)
-template <typename T, int N, int RM>
+// S: element type in memory; T: arithmetic type of the transform.
+template <typename S, typename T, int N, int RM>
 __global__ void __launch_bounds__(kThreads)
-    k_dht_rows(const T* src, T* dst, int nrows, T scale, const int* done, const T* __restrict__ twc,
+    k_dht_rows(const S* src, S* dst, int nrows, T scale, const int* done, const T* __restrict__ twc,
                const T* __restrict__ tws) {
   using F = LineFFT<T, N, RM>;
   if (done != nullptr && *done) return;
@@ -48,26 +80,26 @@ __global__ void __launch_bounds__(kThreads)
   const int p = tid / F::TS, j = tid - p * F::TS;
   const int row0 = 2 * (blockIdx.x * pairs + p);
   const bool valid = row0 < nrows;
-  constexpr int LS = line_stride_words<F::L, true>();
+  constexpr int LS = line_stride_words<T, N, RM, true>();
   T* sr = sm + (size_t)p * 2 * LS;
   T* si = sr + LS;
   T vr[F::R], vi[F::R];
-  const T* s0 = src + (size_t)row0 * N;
+  const S* s0 = src + (size_t)row0 * N;
 #pragma unroll
   for (int q = 0; q < F::R; ++q) {
-    vr[q] = valid ? s0[j + q * F::TS] : T(0);
-    vi[q] = valid ? s0[N + j + q * F::TS] : T(0);
+    vr[q] = valid ? to_compute<T>(s0[j + q * F::TS]) : T(0);
+    vi[q] = valid ? to_compute<T>(s0[N + j + q * F::TS]) : T(0);
   }
   F::run(vr, vi, j, sr, si, twc, tws);
   if (valid) {
-    T* d0 = dst + (size_t)row0 * N;
+    S* d0 = dst + (size_t)row0 * N;
 #pragma unroll
     for (int q = 0; q < F::R; ++q) {
       const int k = j + q * F::TS;
       T h1, h2;
       dht_split(sr, si, k, N, h1, h2);
-      d0[k] = h1 * scale;
-      d0[N + k] = h2 * scale;
+      d0[k] = to_storage<S>(h1 * scale);
+      d0[N + k] = to_storage<S>(h2 * scale);
     }
   }
 }
@@ -76,12 +108,12 @@ __global__ void __launch_bounds__(kThreads)
 // Block: `pairs` pairs of adjacent x-columns (x, x+1) packed as re/im, lines
 // along the strided axis; thread (p, j) = (tid % pairs, tid / pairs) so that a
 // warp reads whole row segments.
-template <typename T, int N, int RM>
+template <typename S, typename T, int N, int RM>
 __global__ void __launch_bounds__(kThreads)
-    k_dht_cols(T* data, size_t line_stride, size_t outer_stride, T scale, const int* done,
+    k_dht_cols(S* data, size_t line_stride, size_t outer_stride, T scale, const int* done,
                const T* __restrict__ twc, const T* __restrict__ tws) {
   using F = LineFFT<T, N, RM>;
-  using V = typename Vec2<T>::type;
+  using V = typename Vec2<S>::type;
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -89,15 +121,15 @@ __global__ void __launch_bounds__(kThreads)
   const int pairs = blockDim.x / F::TS;
   const int p = tid % pairs, j = tid / pairs;
   const size_t base = (size_t)blockIdx.y * outer_stride + (size_t)blockIdx.x * 2 * pairs + 2 * p;
-  constexpr int LS = line_stride_words<F::L, false>();
+  constexpr int LS = line_stride_words<T, N, RM, false>();
   T* sr = sm + (size_t)p * 2 * LS;
   T* si = sr + LS;
   T vr[F::R], vi[F::R];
 #pragma unroll
   for (int q = 0; q < F::R; ++q) {
     const V v = *reinterpret_cast<const V*>(data + base + (size_t)(j + q * F::TS) * line_stride);
-    vr[q] = v.x;
-    vi[q] = v.y;
+    vr[q] = to_compute<T>(v.x);
+    vi[q] = to_compute<T>(v.y);
   }
   F::run(vr, vi, j, sr, si, twc, tws);
 #pragma unroll
@@ -106,8 +138,8 @@ __global__ void __launch_bounds__(kThreads)
     T h1, h2;
     dht_split(sr, si, k, N, h1, h2);
     V o;
-    o.x = h1 * scale;
-    o.y = h2 * scale;
+    o.x = to_storage<S>(h1 * scale);
+    o.y = to_storage<S>(h2 * scale);
     *reinterpret_cast<V*>(data + base + (size_t)k * line_stride) = o;
   }
 }
@@ -130,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
   const int p = tid % pairs, j = tid / pairs;
   const int x = blockIdx.x * 2 * pairs + 2 * p;
   const size_t base = (size_t)blockIdx.y * outer_stride + x;
-  constexpr int LS = line_stride_words<F::L, false>();
+  constexpr int LS = line_stride_words<T, N, RM, false>();
   T* sr = sm + (size_t)p * 2 * LS;
   T* si = sr + LS;
   T vr[F::R], vi[F::R];
@@ -158,8 +190,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const T mu = (c ? mxb : mxa) + ml;
-        const T L = T(1) + s * mu + se2 * mu * mu;
-        const T dd = h[c] / L;
+        const T dd = h[c] * recip_ge1(T(1) + mu * (s + se2 * mu));
         dv[c] = dd;
         acc[0] += h[c] * dd;
         acc[1] += dd * dd;
@@ -169,25 +200,28 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
       // xi holds the transformed part of the residual that is linear in the
       // iterate and not formed by the stencil kernel: -T_h[u - g] (plain
       // FP64) or R_outer - T_h[delta] (inner solve); it advances with the
-      // previous step, xi -= alpha_prev T_h d_prev = alpha_prev dspec / mu.
+      // previous step, xi -= alpha_prev T_h d_prev, where dspec keeps the
+      // transform of T_h d_prev.  With L = lam s + s mu + s eps^2 mu^2 + 1/mu,
+      // d = rt / L = mu rt / P and T_h d = d / mu = rt / P, where
+      // P = 1 + mu (lam s + mu (s + s eps^2 mu)) >= 1: one reciprocal.
       const size_t idx = base + (size_t)k * line_stride;
       const V xv = *reinterpret_cast<const V*>(xi + idx);
       const V dp = *reinterpret_cast<const V*>(dspec + idx);
       const T xs[2] = {xv.x, xv.y}, ds[2] = {dp.x, dp.y};
-      T xn[2];
+      T xn[2], tn[2];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const T mu = (c ? mxb : mxa) + ml;
-        T rt = T(0), dd = T(0), xc = T(0);
+        T rt = T(0), dd = T(0), xc = T(0), td = T(0);
         if (mu > T(0)) {
-          const T imu = T(1) / mu;
-          xc = xs[c] - alpha_prev * ds[c] * imu;
+          xc = xs[c] - alpha_prev * ds[c];
           rt = h[c] + xc;
-          const T L = sl + s * mu + se2 * mu * mu + imu;
-          dd = rt / L;
-          acc[3] += dd * dd * imu;
+          td = rt * recip_ge1(T(1) + mu * (sl + mu * (s + se2 * mu)));
+          dd = mu * td;
+          acc[3] += dd * td;
         }
         xn[c] = xc;
+        tn[c] = td;
         dv[c] = dd;
         acc[0] += rt * dd;
         acc[1] += dd * dd;
@@ -197,8 +231,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
       V xo, o;
       xo.x = xn[0];
       xo.y = xn[1];
-      o.x = dv[0];
-      o.y = dv[1];
+      o.x = tn[0];
+      o.y = tn[1];
       *reinterpret_cast<V*>(xi + idx) = xo;
       *reinterpret_cast<V*>(dspec + idx) = o;
     }
@@ -326,7 +360,7 @@ constexpr int radix_mid() {
 }
 template <typename T, int N, int RM, bool ROWS>
 size_t pair_smem() {
-  return 2 * (size_t)line_stride_words<LineFFT<T, N, RM>::L, ROWS>() * sizeof(T);
+  return 2 * (size_t)line_stride_words<T, N, RM, ROWS>() * sizeof(T);
 }
 
 // Number of column pairs per block: fill 256 threads, bounded by the shared
@@ -340,28 +374,28 @@ int pick_pairs(int avail_pairs) {
   return pairs < 1 ? 1 : pairs;
 }
 
-template <typename T, int N>
-cudaError_t rows_impl(const T* src, T* dst, int nrows, T scale, const int* done, const T* twc,
+template <typename S, typename T, int N>
+cudaError_t rows_impl(const S* src, S* dst, int nrows, T scale, const int* done, const T* twc,
                       const T* tws, cudaStream_t st) {
   constexpr int RM = radix_pass<T>();
   using F = LineFFT<T, N, RM>;
   const int pairs = pick_pairs<T, N, RM, true>(1 << 30);
   const int rows_per_block = 2 * pairs;
   const int grid = (nrows + rows_per_block - 1) / rows_per_block;
-  k_dht_rows<T, N, RM><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, true>(), st>>>(src, dst, nrows, scale, done,
-                                                                               twc, tws);
+  k_dht_rows<S, T, N, RM><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, true>(), st>>>(src, dst, nrows, scale,
+                                                                                  done, twc, tws);
   return cudaGetLastError();
 }
 
-template <typename T, int N>
-cudaError_t cols_impl(T* data, int nx, int nouter, size_t line_stride, size_t outer_stride, T scale,
+template <typename S, typename T, int N>
+cudaError_t cols_impl(S* data, int nx, int nouter, size_t line_stride, size_t outer_stride, T scale,
                       const int* done, const T* twc, const T* tws, cudaStream_t st) {
   constexpr int RM = radix_pass<T>();
   using F = LineFFT<T, N, RM>;
   const int pairs = pick_pairs<T, N, RM, false>(nx / 2);
   dim3 grid(nx / (2 * pairs), nouter);
-  k_dht_cols<T, N, RM><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, false>(), st>>>(data, line_stride, outer_stride,
-                                                                               scale, done, twc, tws);
+  k_dht_cols<S, T, N, RM><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, false>(), st>>>(
+      data, line_stride, outer_stride, scale, done, twc, tws);
   return cudaGetLastError();
 }
 
@@ -409,10 +443,13 @@ cudaError_t mid_impl(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T
 template <typename T, int N>
 void set_attrs() {
   constexpr int RP = radix_pass<T>(), RD = radix_mid<T>();
-  cudaFuncSetAttribute(k_dht_rows<T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_dht_cols<T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_rows<T, T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_cols<T, T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   cudaFuncSetAttribute(k_mid<T, N, 4, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   cudaFuncSetAttribute(k_mid<T, N, 6, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  constexpr int RF = radix_pass<ff>();
+  cudaFuncSetAttribute(k_dht_rows<double, ff, N, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_cols<double, ff, N, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
 }
 
 #define PSD_DISPATCH_N(n, CALL)      \
@@ -433,7 +470,22 @@ void set_attrs() {
 template <typename T>
 cudaError_t launch_dht_rows(const T* src, T* dst, int nx, int nrows, T scale, const int* done,
                             const AxisTables<T>& tb, cudaStream_t st) {
-  PSD_DISPATCH_N(nx, (rows_impl<T, NN>(src, dst, nrows, scale, done, tb.twc[0], tb.tws[0], st)));
+  PSD_DISPATCH_N(nx, (rows_impl<T, T, NN>(src, dst, nrows, scale, done, tb.twc[0], tb.tws[0], st)));
+}
+
+cudaError_t launch_dht_rows_ff(const double* src, double* dst, int nx, int nrows, double scale,
+                               const AxisTables<ff>& tb, cudaStream_t st) {
+  PSD_DISPATCH_N(nx, (rows_impl<double, ff, NN>(src, dst, nrows, ff(scale), nullptr, tb.twc[0], tb.tws[0], st)));
+}
+
+cudaError_t launch_dht_cols_ff(double* data, const KParams& kp, int ax, double scale, const AxisTables<ff>& tb,
+                               cudaStream_t st) {
+  const int n = ax == 1 ? kp.ny : kp.nz;
+  const size_t line_stride = ax == 1 ? (size_t)kp.nx : (size_t)kp.nx * kp.ny;
+  const size_t outer_stride = ax == 1 ? (size_t)kp.nx * kp.ny : (size_t)kp.nx;
+  const int nouter = ax == 1 ? kp.nz : kp.ny;
+  PSD_DISPATCH_N(n, (cols_impl<double, ff, NN>(data, kp.nx, nouter, line_stride, outer_stride, ff(scale), nullptr,
+                                               tb.twc[ax], tb.tws[ax], st)));
 }
 
 template <typename T>
@@ -451,8 +503,8 @@ cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const i
     outer_stride = kp.nx;
     nouter = kp.ny;
   }
-  PSD_DISPATCH_N(n, (cols_impl<T, NN>(data, kp.nx, nouter, line_stride, outer_stride, scale, done,
-                                      tb.twc[ax], tb.tws[ax], st)));
+  PSD_DISPATCH_N(n, (cols_impl<T, T, NN>(data, kp.nx, nouter, line_stride, outer_stride, scale, done,
+                                         tb.twc[ax], tb.tws[ax], st)));
 }
 
 template <typename T>

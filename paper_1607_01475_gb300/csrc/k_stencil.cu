@@ -255,6 +255,8 @@ __global__ void __launch_bounds__(NT)
   comp_lap(z0 - 1);
   comp_lap(z0);
   comp_flux(z0 - 1);
+  // base slot of z0 - 1, read just above, is the one the first step refills
+  if (MODE != RM_PLAIN) __syncthreads();
   for (int z = z0; z < z0 + zc; ++z) {
     load_plane(z + 2);
     load_base(z + 1);

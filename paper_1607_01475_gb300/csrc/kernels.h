@@ -3,11 +3,13 @@
 
 #include <cuda_runtime.h>
 
+#include "ffloat.cuh"
 #include "psd_common.cuh"
 
 namespace psd {
 
-// Per-axis tables owned by a context, in both precisions.
+// Per-axis tables owned by a context: FP64, FP32, and float-float twiddles
+// (no symbols).
 template <typename T>
 struct AxisTables {
   const T* twc[3];  // cos(2 pi t / n_a), t < n_a
@@ -27,14 +29,21 @@ template <typename T>
 cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const int* done,
                             const AxisTables<T>& tb, cudaStream_t st);
 
+// The same passes on FP64 data computed in float-float arithmetic (about 48
+// significant bits; tables of double-word twiddles).
+cudaError_t launch_dht_rows_ff(const double* src, double* dst, int nx, int nrows, double scale,
+                               const AxisTables<ff>& tb, cudaStream_t st);
+cudaError_t launch_dht_cols_ff(double* data, const KParams& kp, int ax, double scale, const AxisTables<ff>& tb,
+                               cudaStream_t st);
+
 // The middle pass along the slowest axis (y in 2D, z in 3D) of the
 // preconditioner: forward DHT, division by the symbol of L_h, Parseval sums
 // into ctrl, inverse DHT (with the 1/N of the whole transform).  Order 6
-// also advances xi -= alpha_prev dspec / mu (xi: the transformed linear part
+// also advances xi -= alpha_prev dspec (xi: the transformed linear part
 // of the residual not formed by the stencil kernel, -T_h[u - g] or
 // R_outer - T_h[delta]), adds it to the transformed local residual, stores
-// the new direction spectrum in dspec and decides convergence on the
-// spectral residual norm.
+// the spectrum of T_h d for the new direction d in dspec and decides
+// convergence on the spectral residual norm.
 template <typename T>
 cudaError_t launch_mid(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* xi, T* dspec,
                        const AxisTables<T>& tb, cudaStream_t st);

@@ -52,13 +52,14 @@ struct psd_context {
   void* tables = nullptr;
   AxisTables<double> tb64{};
   AxisTables<float> tb32{};
+  AxisTables<psd::ff> tbff{};
 
   // FP64 work arrays
   double* ub = nullptr;     // second iterate buffer (ping-pong with the caller's u)
   double* W = nullptr;      // residual / transform work array
   double* D = nullptr;      // search direction
   double* Z = nullptr;      // order 6: plain solve: xi = -DHT(u - g)/mu; mixed: DHT(u - g)
-  double* Dsp = nullptr;    // order 6: DHT spectrum of the last direction
+  double* Dsp = nullptr;    // order 6: DHT spectrum of T_h d for the last direction d
   // FP32 work arrays (mixed)
   float* u32 = nullptr;
   float* da = nullptr;
@@ -176,10 +177,22 @@ psd_status build_tables(psd_context* c) {
     off += n[a];
   }
   for (size_t i = 0; i < tot; ++i) h32[i] = (float)h64[i];
-  CK(cudaMalloc(&c->tables, tot * (sizeof(double) + sizeof(float))));
+  // float-float twiddles: hi = the nearest float, lo = the nearest float to
+  // the remainder, both from the long-double value
+  std::vector<psd::ff> hff(tot);
+  for (int a = 0; a < 3; ++a)
+    for (int t = 0; t < n[a]; ++t)
+      for (int w = 0; w < 2; ++w) {
+        const long double v = w == 0 ? cosl(2.0L * pi * t / n[a]) : sinl(2.0L * pi * t / n[a]);
+        const float hi = (float)v;
+        hff[offs[a][w] + t] = psd::ff(hi, (float)(v - (long double)hi));
+      }
+  CK(cudaMalloc(&c->tables, tot * (sizeof(double) + sizeof(float) + sizeof(psd::ff))));
   double* d64 = (double*)c->tables;
-  float* d32 = (float*)(d64 + tot);
+  psd::ff* dff = (psd::ff*)(d64 + tot);
+  float* d32 = (float*)(dff + tot);
   CK(cudaMemcpy(d64, h64.data(), tot * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dff, hff.data(), tot * sizeof(psd::ff), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d32, h32.data(), tot * sizeof(float), cudaMemcpyHostToDevice));
   for (int a = 0; a < 3; ++a) {
     c->tb64.twc[a] = d64 + offs[a][0];
@@ -188,6 +201,9 @@ psd_status build_tables(psd_context* c) {
     c->tb32.twc[a] = d32 + offs[a][0];
     c->tb32.tws[a] = d32 + offs[a][1];
     c->tb32.sym[a] = d32 + offs[a][2];
+    c->tbff.twc[a] = dff + offs[a][0];
+    c->tbff.tws[a] = dff + offs[a][1];
+    c->tbff.sym[a] = nullptr;
   }
   return PSD_OK;
 }
@@ -282,6 +298,18 @@ psd_status full_dht(psd_context* c, T* x, T scale, const AxisTables<T>& tb) {
   return PSD_OK;
 }
 
+// Full separable DHT of FP64 data in float-float arithmetic (relative error
+// a few 2^-48 against ~2^-53 for FP64 arithmetic, at a fraction of the cost
+// on GB300, whose FP64 rate is 1/64 of its FP32 rate); scale a power of two.
+psd_status full_dht_ff(psd_context* c, double* x, double scale) {
+  const KParams& kp = c->kp;
+  const int nrows = kp.ny * kp.nz;
+  { ProfScope p_(c, PSD_PROF_DHT_ROWS_FF); CK(psd::launch_dht_rows_ff(x, x, kp.nx, nrows, 1.0, c->tbff, c->st)); }
+  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, kp.dim == 2 ? scale : 1.0, c->tbff, c->st)); }
+  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 2, scale, c->tbff, c->st)); }
+  return PSD_OK;
+}
+
 // The search-direction solve L_h d = W of one PSD iteration (W is consumed).
 template <typename T>
 psd_status precond_passes(psd_context* c, T* W, T* D, Ctrl* ctrl, T* xi, T* dspec, const AxisTables<T>& tb) {
@@ -359,7 +387,7 @@ psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f
   TRY(upload_ctrl(c, c->ctrl2, h));
   ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
-  TRY(full_dht<double>(c, c->W, 1.0, c->tb64));
+  TRY(full_dht_ff(c, c->W, 1.0));
   { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec6_combine<double>(c->W, c->Z, kp, c->tb64, c->st)); }
   { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(c->W, c->N, kp.hd * kp.inv_ntot, c->ctrl2, c->partials, c->st)); }
   Ctrl h2;
@@ -448,7 +476,7 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
   if (six) {
     // zeta64 = DHT(u0 - g), advanced with DHT(delta) after every correction
     { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
-    TRY(full_dht<double>(c, c->Z, 1.0, c->tb64));
+    TRY(full_dht_ff(c, c->Z, 1.0));
   }
   int inner_total = 0, outer = 0;
   int status = PSD_ERR_NOCONV;
@@ -458,9 +486,9 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
     if (delta) {
       { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, delta, c->u32, c->N, c->st)); }
       if (six) {
-        // zeta64 += DHT(delta), in FP64
+        // zeta64 += DHT(delta)
         { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_widen_f64(c->D, delta, c->N, c->st)); }
-        TRY(full_dht<double>(c, c->D, 1.0, c->tb64));
+        TRY(full_dht_ff(c, c->D, 1.0));
         { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, c->Z, c->D, 1.0, 1.0, 0.0, c->N, c->st)); }
         // keep mean(u) = mean(g) exactly: delta is mean-zero only up to FP32 rounding
         Ctrl hu;
@@ -611,11 +639,8 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
   kp.inv_ntot = 1.0 / (double)c->N;
   psd::finish_kparams(kp);
   c->pk = (params->p == 4.0) ? psd::PK_4 : psd::PK_GEN;
-  static bool attrs = false;
-  if (!attrs) {
-    psd::init_dht_attributes();
-    attrs = true;
-  }
+  static const bool attrs = (psd::init_dht_attributes(), true);  // once, thread-safe
+  (void)attrs;
   auto bail = [&](psd_status st) {
     g_create_error = c->err;
     psd_destroy(c);
@@ -669,6 +694,12 @@ psd_status psd_profile(psd_handle c, int enable) {
       c->prof_n[k] = 0;
       c->prof_durs[k].clear();
     }
+    // create the whole event pool now rather than while kernels are queued
+    while (c->ev_pool.size() < 4096) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      c->ev_pool.push_back(e);
+    }
   } else {
     TRY(prof_flush(c));
   }
@@ -699,7 +730,8 @@ psd_status psd_profile_read(psd_handle c, double* ms, long long* launches, doubl
 const char* psd_profile_class_name(int k) {
   static const char* names[PSD_PROF_CLASSES] = {
       "residual_fp64", "residual_fp32", "dht_rows_fp64", "dht_rows_fp32", "dht_cols_fp64", "dht_cols_fp32",
-      "mid_fp64",      "mid_fp32",      "linesearch_fp64", "linesearch_fp32", "other"};
+      "mid_fp64",      "mid_fp32",      "linesearch_fp64", "linesearch_fp32", "other",
+      "dht_rows_ff",   "dht_cols_ff"};
   return (k >= 0 && k < PSD_PROF_CLASSES) ? names[k] : nullptr;
 }
 

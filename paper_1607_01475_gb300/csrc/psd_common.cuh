@@ -178,4 +178,16 @@ __device__ __forceinline__ int wrapi(int i, int n) {  // n a power of two
   return i & (n - 1);
 }
 
+// 1/x for finite x >= 1 (the preconditioner symbols).  FP32: the hardware
+// reciprocal estimate (rcp.approx) refined by one Newton-Raphson step
+// r <- r + r (1 - x r), which squares the estimate's relative error, so the
+// result is within an ulp or so of 1/x; x >= 1 keeps it clear of
+// denormals.  FP64: the IEEE quotient.
+__device__ __forceinline__ float recip_ge1(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+__device__ __forceinline__ double recip_ge1(double x) { return 1.0 / x; }
+
 }  // namespace psd

@@ -147,3 +147,30 @@ def workload_spfc(shape=(256, 256, 256)):
     u0 = np.full(shape, g.mean())
     return dict(order=6, shape=tuple(shape), L=TWO_PI, p=4.0, s=0.05, eps=0.1,
                 lam=1.0, f=f, g=g, u0=u0)
+
+
+def workload_batch(count=96, max_exp=5):
+    """Uneven 2D fourth-order instances on (0, 2pi)^2: n = 2^(6 + floor(max_exp U))
+    (64..1024 for max_exp = 5), s = 10^(-3 + 2U), eps uniform in [0.02, 0.2],
+    p = 3 or 4 with probability 1/2, f a Fourier field with K = 8; u0 = 0.
+
+    ``tol`` is the instance's residual target: 1e-10, raised to the FP64
+    rounding floor of the residual where that is larger.  Delta_h^2 applied
+    as two Laplacian passes carries a rounding error of about
+    64 eps64 |u| per cell, scaled by s eps^2 / h^4, so
+    floor = 64 eps64 (s eps^2 / h^4) max|f| |Omega|^(1/2) (|u| <= max|f|
+    for these problems)."""
+    out = []
+    for i in range(count):
+        u = uniform(seed_for(3, i, 5), 4)
+        n = 2 ** (6 + int(np.floor(max_exp * u[0])))
+        s = 10.0 ** (-3.0 + 2.0 * u[1])
+        eps = 0.02 + 0.18 * u[2]
+        p = 3.0 if u[3] < 0.5 else 4.0
+        shape = (n, n)
+        f = fourier_field(shape, TWO_PI, 8, seed_for(3, i, 0))
+        h = TWO_PI / n
+        floor = 64.0 * np.finfo(np.float64).eps * (s * eps * eps / h ** 4) * float(np.max(np.abs(f))) * TWO_PI
+        out.append(dict(order=4, shape=shape, L=TWO_PI, p=p, s=s, eps=eps, lam=0.0, f=f, g=None,
+                        u0=np.zeros(shape), tol=max(1e-10, floor)))
+    return out
