@@ -21,6 +21,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstring>
+
 namespace psd {
 
 struct __align__(8) ff {
@@ -31,62 +34,198 @@ struct __align__(8) ff {
   __host__ __device__ constexpr explicit ff(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
 };
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+// Round-to-nearest FP32 primitives: the intrinsics on the device (never
+// contracted into FMAs), plain IEEE operations on the host (built without
+// contraction).
+__host__ __device__ __forceinline__ float f_add(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ float f_sub(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+__host__ __device__ __forceinline__ float f_mul(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ float f_fma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return fmaf(a, b, c);
+#endif
 }
 
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
+__host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = f_add(a, b);
+  const float bb = f_sub(s, a);
+  e = f_add(f_sub(a, f_sub(s, bb)), f_sub(b, bb));
 }
 
-__device__ __forceinline__ ff ff_add(ff x, ff y) {
+__host__ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = f_add(a, b);
+  e = f_sub(b, f_sub(s, a));
+}
+
+__host__ __device__ __forceinline__ ff ff_add(ff x, ff y) {
   float sh, sl, th, tl, vh, vl;
   two_sum(x.hi, y.hi, sh, sl);
   two_sum(x.lo, y.lo, th, tl);
-  const float c = __fadd_rn(sl, th);
+  const float c = f_add(sl, th);
   fast_two_sum(sh, c, vh, vl);
-  const float w = __fadd_rn(tl, vl);
+  const float w = f_add(tl, vl);
   ff z;
   fast_two_sum(vh, w, z.hi, z.lo);
   return z;
 }
 
-__device__ __forceinline__ ff ff_neg(ff x) { return ff(-x.hi, -x.lo); }
-__device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+__host__ __device__ __forceinline__ ff ff_neg(ff x) { return ff(-x.hi, -x.lo); }
+__host__ __device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
 
-__device__ __forceinline__ ff ff_mul(ff x, ff y) {
-  const float ch = __fmul_rn(x.hi, y.hi);
-  const float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
-  const float tl0 = __fmul_rn(x.lo, y.lo);
-  const float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
-  const float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
-  const float cl3 = __fadd_rn(cl1, cl2);
+__host__ __device__ __forceinline__ ff ff_mul(ff x, ff y) {
+  const float ch = f_mul(x.hi, y.hi);
+  const float cl1 = f_fma(x.hi, y.hi, -ch);
+  const float tl0 = f_mul(x.lo, y.lo);
+  const float tl1 = f_fma(x.hi, y.lo, tl0);
+  const float cl2 = f_fma(x.lo, y.hi, tl1);
+  const float cl3 = f_add(cl1, cl2);
   ff z;
   fast_two_sum(ch, cl3, z.hi, z.lo);
   return z;
 }
 
-__device__ __forceinline__ ff ff_mul_f(ff x, float y) {
-  const float ch = __fmul_rn(x.hi, y);
-  const float cl1 = __fmaf_rn(x.hi, y, -ch);
-  const float cl3 = __fmaf_rn(x.lo, y, cl1);
+__host__ __device__ __forceinline__ ff ff_mul_f(ff x, float y) {
+  const float ch = f_mul(x.hi, y);
+  const float cl1 = f_fma(x.hi, y, -ch);
+  const float cl3 = f_fma(x.lo, y, cl1);
   ff z;
   fast_two_sum(ch, cl3, z.hi, z.lo);
   return z;
 }
 
 // Exact scaling by a power of two.
-__device__ __forceinline__ ff ff_scale2(ff x, float p2) { return ff(x.hi * p2, x.lo * p2); }
+__host__ __device__ __forceinline__ ff ff_scale2(ff x, float p2) { return ff(x.hi * p2, x.lo * p2); }
 
 __host__ __device__ __forceinline__ double ff_to_double(ff v) { return (double)v.hi + (double)v.lo; }
 
+// ---- conversions between FP64 and float-float by bit manipulation (no FP64
+// arithmetic, whose pipe is 1/64 of the FP32 rate on GB300)
+__host__ __device__ __forceinline__ unsigned long long ff_dbits(double v) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long b;
+  std::memcpy(&b, &v, 8);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ double ff_bitsd(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double v;
+  std::memcpy(&v, &b, 8);
+  return v;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned ff_fbits(float v) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(v);
+#else
+  unsigned b;
+  std::memcpy(&b, &v, 4);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float ff_bitsf(unsigned b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float v;
+  std::memcpy(&v, &b, 4);
+  return v;
+#endif
+}
+
+// double -> float-float: hi = v truncated to 24 significant bits, lo = the
+// remaining 29 bits rounded to a float, then renormalised (hi + lo = v to a
+// relative 2^-47).  Magnitudes below the float normal range give 0 (with
+// the sign), above it +-inf; NaN stays NaN.
+__host__ __device__ __forceinline__ ff ff_from_double_bits(double v) {
+  const unsigned long long b = ff_dbits(v);
+  const unsigned sgn = (unsigned)(b >> 63) << 31;
+  const int E = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+  if (E == 0x7FF) return ff(ff_bitsf(sgn | 0x7F800000u | (m ? 0x400000u : 0u)), 0.0f);
+  const int e = E - 1023;
+  if (e < -126) return ff(ff_bitsf(sgn), 0.0f);
+  if (e > 127) return ff(ff_bitsf(sgn | 0x7F800000u), 0.0f);
+  const float hi = ff_bitsf(sgn | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+  const unsigned r = (unsigned)(m & 0x1FFFFFFFu);  // the remainder is r 2^(e - 52)
+  if (r == 0) return ff(hi, 0.0f);
+#ifdef __CUDA_ARCH__
+  const float rf = __uint2float_rn(r);
+#else
+  const float rf = (float)r;
+#endif
+  float lo = (rf * ff_bitsf(0x25800000u)) * ff_bitsf((unsigned)(e + 127) << 23);  // r 2^-52 2^e
+  if (sgn) lo = -lo;
+  ff z;
+  fast_two_sum(hi, lo, z.hi, z.lo);
+  return z;
+}
+
+// float-float -> double, hi + lo assembled as a 53-bit integer significand
+// (exact for a normalised pair up to the truncation of bits of lo below
+// 2^-53 of hi; lo may be subnormal).  A zero or subnormal hi gives a signed
+// zero.
+__host__ __device__ __forceinline__ double ff_to_double_bits(ff x) {
+  const unsigned hb = ff_fbits(x.hi), lb = ff_fbits(x.lo);
+  const unsigned long long sgn = (unsigned long long)(hb >> 31) << 63;
+  const int eh = (int)((hb >> 23) & 0xFF);
+  if (eh == 0) return ff_bitsd(sgn);
+  if (eh == 0xFF) return ff_bitsd(sgn | (0x7FFULL << 52) | ((hb & 0x7FFFFFu) ? (1ULL << 51) : 0ULL));
+  long long n = (long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;  // in units of 2^(eh - 127 - 52)
+  int el = (int)((lb >> 23) & 0xFF);
+  if (el != 0xFF && (lb & 0x7FFFFFFFu) != 0) {
+    // in units of 2^(el - 127 - 23); a subnormal lo has no implicit bit and el = 1
+    const long long ml = (long long)((lb & 0x7FFFFFu) | (el ? 0x800000u : 0u));
+    if (el == 0) el = 1;
+    const int sh = el - eh + 29;
+    long long t = 0;
+    if (sh >= 0)
+      t = sh < 32 ? ml << sh : 0;
+    else if (sh > -25)
+      t = ml >> (-sh);
+    n += ((lb ^ hb) >> 31) ? -t : t;
+  }
+  int e = eh - 127;
+  while (n >= (1LL << 53)) {
+    n >>= 1;
+    ++e;
+  }
+  while (n > 0 && n < (1LL << 52)) {
+    n <<= 1;
+    --e;
+  }
+  if (n <= 0) return ff_bitsd(sgn);
+  return ff_bitsd(sgn | ((unsigned long long)(e + 1023) << 52) | ((unsigned long long)n & 0xFFFFFFFFFFFFFULL));
+}
+
 // Arithmetic operators so that the line-FFT templates run on ff.
-__device__ __forceinline__ ff operator+(ff a, ff b) { return ff_add(a, b); }
-__device__ __forceinline__ ff operator-(ff a, ff b) { return ff_sub(a, b); }
-__device__ __forceinline__ ff operator-(ff a) { return ff_neg(a); }
-__device__ __forceinline__ ff operator*(ff a, ff b) { return ff_mul(a, b); }
+__host__ __device__ __forceinline__ ff operator+(ff a, ff b) { return ff_add(a, b); }
+__host__ __device__ __forceinline__ ff operator-(ff a, ff b) { return ff_sub(a, b); }
+__host__ __device__ __forceinline__ ff operator-(ff a) { return ff_neg(a); }
+__host__ __device__ __forceinline__ ff operator*(ff a, ff b) { return ff_mul(a, b); }
 
 }  // namespace psd

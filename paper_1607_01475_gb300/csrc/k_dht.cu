@@ -32,8 +32,12 @@ __device__ __forceinline__ S to_storage(C v) {
   return S(v);
 }
 template <>
+__device__ __forceinline__ ff to_compute<ff, double>(double v) {
+  return ff_from_double_bits(v);
+}
+template <>
 __device__ __forceinline__ double to_storage<double, ff>(ff v) {
-  return ff_to_double(v);
+  return ff_to_double_bits(v);
 }
 
 constexpr int kThreads = 256;
@@ -176,7 +180,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
 
   const T mo = (symo != nullptr) ? symo[blockIdx.y] : T(0);
   const T mxa = symx[x] + mo, mxb = symx[x + 1] + mo;
-  const T s = (T)kp.s, se2 = (T)(kp.s * kp.eps2), sl = (T)(kp.s * kp.lam);
+  const KConst<T>& C = kconst<T>(kp);
+  const T s = C.s, se2 = C.se2, sl = C.sl;
   const T alpha_prev = (ORDER == 6) ? (T)ctrl->alpha : T(0);
   T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
   }
   __syncthreads();  // every thread has read the forward spectrum
   F::run(vr, vi, j, sr, si, twc, tws);
-  const T scale = (T)kp.inv_ntot;
+  const T scale = C.inv_ntot;
 #pragma unroll
   for (int q = 0; q < F::R; ++q) {
     const int k = j + q * F::TS;

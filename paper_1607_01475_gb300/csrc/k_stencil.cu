@@ -137,9 +137,10 @@ __global__ void __launch_bounds__(NT)
   const size_t plane = (size_t)nx * ny;
   const bool upd = a.d != nullptr;
   const T alpha = upd ? (T)ctrl->alpha : T(0);
-  const T ih = (T)kp.inv_h, ih2 = ih * ih, q4 = T(0.25) * ih;
-  const T s = (T)kp.s, se2 = (T)(kp.s * kp.eps2), cu = (T)kp.cu;
-  const T beta = (T)(0.5 * (kp.p - 2.0));
+  const KConst<T>& C = kconst<T>(kp);
+  const T ih = C.inv_h, ih2 = ih * ih, q4 = T(0.25) * ih;
+  const T s = C.s, se2 = C.se2, cu = C.cu;
+  const T beta = C.beta;
 
   auto uslot = [&](int zz) { return (zz - z0 + 2) % 5; };
   auto lslot = [&](int zz) { return (zz - z0 + 1) % 3; };
@@ -299,9 +300,10 @@ __global__ void __launch_bounds__(NT) k_res2d(ResArgs<T> a, KParams kp, Ctrl* ct
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const bool upd = a.d != nullptr;
   const T alpha = upd ? (T)ctrl->alpha : T(0);
-  const T ih = (T)kp.inv_h, ih2 = ih * ih, q2 = T(0.5) * ih;
-  const T s = (T)kp.s, se2 = (T)(kp.s * kp.eps2), cu = (T)kp.cu;
-  const T beta = (T)(0.5 * (kp.p - 2.0));
+  const KConst<T>& C = kconst<T>(kp);
+  const T ih = C.inv_h, ih2 = ih * ih, q2 = T(0.5) * ih;
+  const T s = C.s, se2 = C.se2, cu = C.cu;
+  const T beta = C.beta;
 
   for (int idx = tid; idx < SX * SY; idx += NT) {
     const int ly = idx / SX, lx = idx - ly * SX;
@@ -506,6 +508,7 @@ __device__ void linesearch_epilogue(Ctrl* ctrl, const KParams& kp, const double 
 }  // namespace
 }  // namespace psd
 #include "stencil3d_col.cuh"
+#include "stencil3d_rb.cuh"
 namespace psd {
 namespace {
 
@@ -526,7 +529,7 @@ __global__ void __launch_bounds__(NT)
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
   const size_t plane = (size_t)nx * ny;
-  const T beta = (T)(0.5 * (kp.p - 2.0)), pm2 = (T)(kp.p - 2.0);
+  const T beta = kconst<T>(kp).beta, pm2 = kconst<T>(kp).pm2;
   const T trial = (PK == PK_4) ? T(0) : (T)ctrl->alpha;
   auto load = [&](int zz) {
     const int sl_ = (zz - z0) & 1;
@@ -589,7 +592,7 @@ __global__ void __launch_bounds__(NT)
   const int SX = TX + 1, SY = TY + 1;
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const T beta = (T)(0.5 * (kp.p - 2.0)), pm2 = (T)(kp.p - 2.0);
+  const T beta = kconst<T>(kp).beta, pm2 = kconst<T>(kp).pm2;
   const T trial = (PK == PK_4) ? T(0) : (T)ctrl->alpha;
   for (int idx = tid; idx < SX * SY; idx += NT) {
     const int ly = idx / SX, lx = idx - ly * SX;
@@ -695,21 +698,56 @@ int pick_zc(int nz, int nblk_xy) {
   return zc;
 }
 
+// Launch geometry of the residual kernels.  3D FP32 grids large enough to
+// fill the GPU with 32 x 32 tiles take the register-blocked kernel (the FP32
+// residual is bound by shared-memory traffic); FP64 keeps the column kernel
+// (bound by its FP64 operations); small tiles take the general kernel.
+enum ResKind { RK_2D, RK_SMALL3D, RK_COL, RK_RB4 };
+struct ResGeom {
+  int kind;
+  dim3 grid;
+  int zc;
+};
+ResGeom res_geometry(const KParams& kp, bool fp32) {
+  ResGeom g{RK_2D, dim3(1, 1, 1), 1};
+  if (kp.dim != 3) {
+    const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY2 ? kp.ny : BY2;
+    g.grid = dim3(kp.nx / TX, kp.ny / TY);
+    return g;
+  }
+  if (fp32 && kp.nx % 32 == 0 && kp.ny % 32 == 0 && kp.nz >= 16 &&
+      (long long)(kp.nx / 32) * (kp.ny / 32) * (kp.nz / 16) >= 2 * 152) {
+    const int gx = kp.nx / 32, gy = kp.ny / 32;
+    int zc = kp.nz;  // marches of at least 16 planes; about three CTAs per SM
+    while (zc > 16 && (long long)gx * gy * (kp.nz / zc) < 3 * 152) zc >>= 1;
+    g.kind = RK_RB4;
+    g.grid = dim3(gx, gy, kp.nz / zc);
+    g.zc = zc;
+    return g;
+  }
+  const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY3 ? kp.ny : BY3;
+  const int gx = kp.nx / TX, gy = kp.ny / TY;
+  g.zc = pick_zc(kp.nz, gx * gy);
+  g.grid = dim3(gx, gy, kp.nz / g.zc);
+  g.kind = (kp.nx >= 32 && kp.ny >= 8) ? RK_COL : RK_SMALL3D;
+  return g;
+}
+
 template <typename T, int PK, int MODE>
 cudaError_t res_impl(const ResArgs<T>& a, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st) {
-  if (kp.dim == 3) {
-    const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY3 ? kp.ny : BY3;
-    const int gx = kp.nx / TX, gy = kp.ny / TY;
-    const int zc = pick_zc(kp.nz, gx * gy);
-    dim3 grid(gx, gy, kp.nz / zc);
-    if (kp.nx >= 32 && kp.ny >= 8)
-      k_res3d_col<T, PK, MODE><<<grid, NT, 0, st>>>(a, kp, ctrl, partials, zc);
-    else
-      k_res3d<T, PK, MODE><<<grid, NT, 0, st>>>(a, kp, ctrl, partials, zc);
-  } else {
-    const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY2 ? kp.ny : BY2;
-    dim3 grid(kp.nx / TX, kp.ny / TY);
-    k_res2d<T, PK, MODE><<<grid, NT, 0, st>>>(a, kp, ctrl, partials);
+  const ResGeom g = res_geometry(kp, sizeof(T) == 4);
+  switch (g.kind) {
+    case RK_RB4:
+      if constexpr (sizeof(T) == 4) k_res3d_rb<T, PK, MODE, 4><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
+      break;
+    case RK_COL:
+      k_res3d_col<T, PK, MODE><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
+      break;
+    case RK_SMALL3D:
+      k_res3d<T, PK, MODE><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
+      break;
+    default:
+      k_res2d<T, PK, MODE><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials);
   }
   return cudaGetLastError();
 }
@@ -751,15 +789,9 @@ cudaError_t launch_residual(const ResArgs<T>& a, int mode, int pk, const KParams
   return res_impl<T, PK_GEN, RM_PLAIN>(a, kp, ctrl, partials, st);
 }
 
-long long residual_grid_blocks(const KParams& kp) {
-  if (kp.dim == 3) {
-    const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY3 ? kp.ny : BY3;
-    const int gx = kp.nx / TX, gy = kp.ny / TY;
-    const int zc = pick_zc(kp.nz, gx * gy);
-    return (long long)gx * gy * (kp.nz / zc);
-  }
-  const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY2 ? kp.ny : BY2;
-  return (long long)(kp.nx / TX) * (kp.ny / TY);
+long long residual_grid_blocks(const KParams& kp, bool fp32) {
+  const ResGeom g = res_geometry(kp, fp32);
+  return (long long)g.grid.x * g.grid.y * g.grid.z;
 }
 
 template <typename T>

@@ -91,9 +91,9 @@ template <typename T>
 cudaError_t launch_linesearch(const T* u, const T* ubase, const T* d, int pk, const KParams& kp,
                               Ctrl* ctrl, double* partials, cudaStream_t st);
 
-// Number of blocks launch_residual uses for this problem size (one partial
-// sum record per block).
-long long residual_grid_blocks(const KParams& kp);
+// Number of blocks launch_residual<T> uses for this problem size (one
+// partial sum record per block); fp32 = (T is float).
+long long residual_grid_blocks(const KParams& kp, bool fp32);
 
 // ------------------------------------------------------------------ misc
 // y = a * x + b * z + c elementwise (x or z may be null = 0; may alias y).

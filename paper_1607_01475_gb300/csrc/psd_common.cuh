@@ -49,6 +49,18 @@ struct Ctrl {
 };
 
 // Problem scalars passed by value to the kernels.
+// Constants of the operator in a kernel's arithmetic type, formed once on
+// the host.  (Formed in a kernel from the FP64 parameters, a value such as
+// (float)(s * eps2) may be recomputed inside unrolled loops when registers
+// are short, and GB300 issues FP64 at 1/64 of the FP32 rate.)
+template <typename T>
+struct KConst {
+  T s, se2, sl, cu;  // s, s eps^2, s lambda, coefficient of u
+  T cdiv, cbih;      // see KParams
+  T inv_h, inv_ntot;
+  T beta, pm2;       // (p - 2) / 2, p - 2
+};
+
 struct KParams {
   int nx, ny, nz;       // cells per axis (nz = 1 in 2D)
   int dim;
@@ -65,7 +77,20 @@ struct KParams {
   double q;             // 1 / (2^(d-1) h): g = q G
   double cdiv;          // s q^p: s d.(|g|^{p-2} g) = cdiv * (sum of differences of |G|^{p-2} G)
   double cbih;          // s eps^2 / h^4: s eps^2 Delta_h^2 u = cbih * (h^4 Delta_h^2 u)
+  KConst<double> c64;   // the constants in FP64 and FP32 (finish_kparams)
+  KConst<float> c32;
 };
+
+template <typename T>
+__device__ __forceinline__ const KConst<T>& kconst(const KParams& kp);
+template <>
+__device__ __forceinline__ const KConst<double>& kconst<double>(const KParams& kp) {
+  return kp.c64;
+}
+template <>
+__device__ __forceinline__ const KConst<float>& kconst<float>(const KParams& kp) {
+  return kp.c32;
+}
 
 // Fill the derived constants of KParams (host side).
 inline void finish_kparams(KParams& kp) {
@@ -73,6 +98,28 @@ inline void finish_kparams(KParams& kp) {
   const double qp = (kp.p == 4.0) ? kp.q * kp.q * kp.q * kp.q : std::pow(kp.q, kp.p);
   kp.cdiv = kp.s * qp;
   kp.cbih = kp.s * kp.eps2 * kp.inv_h * kp.inv_h * kp.inv_h * kp.inv_h;
+  KConst<double>& d = kp.c64;
+  d.s = kp.s;
+  d.se2 = kp.s * kp.eps2;
+  d.sl = kp.s * kp.lam;
+  d.cu = kp.cu;
+  d.cdiv = kp.cdiv;
+  d.cbih = kp.cbih;
+  d.inv_h = kp.inv_h;
+  d.inv_ntot = kp.inv_ntot;
+  d.beta = 0.5 * (kp.p - 2.0);
+  d.pm2 = kp.p - 2.0;
+  KConst<float>& f = kp.c32;
+  f.s = (float)d.s;
+  f.se2 = (float)d.se2;
+  f.sl = (float)d.sl;
+  f.cu = (float)d.cu;
+  f.cdiv = (float)d.cdiv;
+  f.cbih = (float)d.cbih;
+  f.inv_h = (float)d.inv_h;
+  f.inv_ntot = (float)d.inv_ntot;
+  f.beta = (float)d.beta;
+  f.pm2 = (float)d.pm2;
 }
 
 // ------------------------------------------------------------------ reductions

@@ -80,7 +80,7 @@ extern "C" psd_status psd_residual_noalloc(const psd_params* prm, const double* 
   kp.hd = prm->dim == 3 ? prm->h * prm->h * prm->h : prm->h * prm->h;
   kp.inv_ntot = 1.0 / ((double)kp.nx * kp.ny * kp.nz);
   psd::finish_kparams(kp);
-  const long long blocks = psd::residual_grid_blocks(kp);
+  const long long blocks = psd::residual_grid_blocks(kp, false);
   if (blocks > kMaxBlocks) {
     char buf[160];
     std::snprintf(buf, sizeof buf, "grid needs %lld residual blocks; the static scratch holds %d", blocks,

@@ -63,8 +63,9 @@ __global__ void __launch_bounds__(256, 2)
   const size_t plane = (size_t)nx * ny;
   const bool upd = a.d != nullptr;
   const T alpha = upd ? (T)ctrl->alpha : T(0);
-  const T cdiv = (T)kp.cdiv, cbih = (T)kp.cbih, cu = (T)kp.cu;
-  const T beta = (T)(0.5 * (kp.p - 2.0));
+  const KConst<T>& C = kconst<T>(kp);
+  const T cdiv = C.cdiv, cbih = C.cbih, cu = C.cu;
+  const T beta = C.beta;
 
   // this thread's U-tile elements (flattened e = tid, tid + 256) and where
   // they land in the halo-1 P/M tile
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(256, 3)
   const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
   const size_t plane = (size_t)nx * ny;
-  const T beta = (T)(0.5 * (kp.p - 2.0)), pm2 = (T)(kp.p - 2.0);
+  const T beta = kconst<T>(kp).beta, pm2 = kconst<T>(kp).pm2;
   const T trial = (PK == PK_4) ? T(0) : (T)ctrl->alpha;
   int off[2];
   bool val[2];

@@ -1,0 +1,85 @@
+// Host check of the float-float primitives used by the FP64-storage DHT
+// passes: conversions to and from FP64 by bit manipulation, and the
+// double-word sum and product, against long-double arithmetic.  Built and
+// run by tests/test_ffloat.py (no GPU needed).  Exit status 0 = pass.
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstdint>
+
+#include "../paper_1607_01475_gb300/csrc/ffloat.cuh"
+
+using psd::ff;
+
+static uint64_t rng_state = 0x1607014750ULL;
+static uint64_t next_u64() {  // SplitMix64
+  uint64_t z = (rng_state += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+static double uniform() { return (double)(next_u64() >> 11) * 0x1p-53; }
+// random double: sign, decade in [lo_e, hi_e], full 53-bit mantissa
+static double rand_double(int lo_e, int hi_e) {
+  const double m = 1.0 + uniform();
+  const int e = lo_e + (int)(uniform() * (hi_e - lo_e + 1));
+  const double v = std::ldexp(m, e);
+  return (next_u64() & 1) ? -v : v;
+}
+static long double exact(ff x) { return (long double)x.hi + (long double)x.lo; }
+static bool normalised(ff x) {
+  if (x.hi == 0.0f) return x.lo == 0.0f;
+  const float ulp = std::nextafter(std::fabs(x.hi), INFINITY) - std::fabs(x.hi);
+  return std::fabs(x.lo) <= 0.5f * ulp;
+}
+
+int main() {
+  int fails = 0;
+  double worst_rt = 0, worst_split = 0, worst_add = 0, worst_mul = 0, worst_back = 0;
+  for (int t = 0; t < 200000; ++t) {
+    const double v = rand_double(-100, 100);
+    const ff a = psd::ff_from_double_bits(v);
+    if (!normalised(a)) ++fails;
+    const double rel_split = (double)(std::fabs(exact(a) - (long double)v) / std::fabs((long double)v));
+    if (rel_split > worst_split) worst_split = rel_split;
+    const double back = psd::ff_to_double_bits(a);
+    const double rel_rt = std::fabs(back - v) / std::fabs(v);
+    if (rel_rt > worst_rt) worst_rt = rel_rt;
+    // to double: within one ulp of the exact hi + lo
+    const long double ex = exact(a);
+    const double rel_b = (double)(std::fabs((long double)back - ex) / std::fabs(ex));
+    if (rel_b > worst_back) worst_back = rel_b;
+    // sum and product of two double-words
+    const ff b = psd::ff_from_double_bits(rand_double(-30, 30));
+    const ff c = psd::ff_from_double_bits(rand_double(-30, 30));
+    const ff s = psd::ff_add(b, c), p = psd::ff_mul(b, c);
+    const long double es = exact(b) + exact(c), ep = exact(b) * exact(c);
+    if (es != 0) {
+      const double r = (double)(std::fabs(exact(s) - es) / std::fabs(es));
+      if (r > worst_add) worst_add = r;
+    }
+    const double rp = (double)(std::fabs(exact(p) - ep) / std::fabs(ep));
+    if (rp > worst_mul) worst_mul = rp;
+    if (!normalised(s) || !normalised(p)) ++fails;
+  }
+  // special values
+  if (psd::ff_to_double_bits(psd::ff_from_double_bits(0.0)) != 0.0) ++fails;
+  if (!std::isinf(psd::ff_to_double_bits(psd::ff_from_double_bits(1e300)))) ++fails;
+  if (!std::isnan(psd::ff_to_double_bits(psd::ff_from_double_bits(NAN)))) ++fails;
+  if (psd::ff_to_double_bits(psd::ff_from_double_bits(-1e-300)) != 0.0) ++fails;
+  if (std::signbit(psd::ff_to_double_bits(psd::ff_from_double_bits(-1e-300))) == 0) ++fails;
+  // exact values: powers of two and small integers survive the round trip
+  for (int k = -120; k <= 120; ++k) {
+    const double v = std::ldexp(1.0, k) * 3.0;
+    if (psd::ff_to_double_bits(psd::ff_from_double_bits(v)) != v) ++fails;
+  }
+  const double u2 = 0x1p-48;
+  std::printf("split %.3g  roundtrip %.3g  to_double %.3g  add %.3g  mul %.3g  (units of 2^-48: %.2f %.2f %.2f %.2f %.2f)\n",
+              worst_split, worst_rt, worst_back, worst_add, worst_mul, worst_split / u2, worst_rt / u2,
+              worst_back / u2, worst_add / u2, worst_mul / u2);
+  if (worst_split > 0x1p-47 || worst_rt > 0x1p-47 || worst_back > 0x1p-52 || worst_add > 4 * u2 ||
+      worst_mul > 6 * u2)
+    ++fails;
+  std::printf("%s (%d failures)\n", fails ? "FAIL" : "OK", fails);
+  return fails ? 1 : 0;
+}

@@ -85,6 +85,25 @@ def test_residual_f32_kernel(oracle, shape):
     assert rel(host(r).astype(np.float64), ref) <= 2e-5
 
 
+# 8 x 8 x 8 CTAs of 32 x 32 x 16 cells: large enough for the register-blocked
+# FP32 residual kernel (which needs at least 2 x 152 such CTAs)
+RB_SHAPE = (128, 256, 256)
+
+
+@pytest.mark.parametrize("p", [4.0, 3.0])
+def test_residual_f32_register_blocked(oracle, p):
+    """The register-blocked FP32 residual kernel against the FP64 oracle on
+    a grid that selects it; the bound of the column kernel."""
+    P, h = _problem(oracle, 4, RB_SHAPE, p)
+    u = smooth_random(RB_SHAPE, seed=3).astype(np.float32)
+    f = smooth_random(RB_SHAPE, seed=4).astype(np.float32)
+    S = Solver(4, RB_SHAPE, h, p, P.s, P.eps)
+    r = torch.empty(RB_SHAPE, dtype=torch.float32, device="cuda")
+    S.residual_f32(torch.from_numpy(u).cuda(), torch.from_numpy(f).cuda(), r)
+    ref = oracle.residual4(u.astype(np.float64), f.astype(np.float64), P)
+    assert rel(host(r).astype(np.float64), ref) <= 2e-5
+
+
 # ---------------------------------------------------------- preconditioner
 
 @pytest.mark.parametrize("shape", SHAPES)
