@@ -36,6 +36,10 @@ __device__ __forceinline__ ff to_compute<ff, double>(double v) {
   return ff_from_double_bits(v);
 }
 template <>
+__device__ __forceinline__ ff to_compute<ff, float>(float v) {
+  return ff(v, 0.0f);
+}
+template <>
 __device__ __forceinline__ double to_storage<double, ff>(ff v) {
   return ff_to_double_bits(v);
 }
@@ -70,10 +74,10 @@ __host__ __device__ constexpr int line_stride_words() {
 constexpr size_t kMaxSmem = 96 * 1024;
 
 // -------------------------------------------------------------- x (rows)
-// S: element type in memory; T: arithmetic type of the transform.
-template <typename S, typename T, int N, int RM>
+// S: element type in memory (SI of the source); T: arithmetic type.
+template <typename S, typename T, int N, int RM, typename SI = S>
 __global__ void __launch_bounds__(kThreads)
-    k_dht_rows(const S* src, S* dst, int nrows, T scale, const int* done, const T* __restrict__ twc,
+    k_dht_rows(const SI* src, S* dst, int nrows, T scale, const int* done, const T* __restrict__ twc,
                const T* __restrict__ tws) {
   using F = LineFFT<T, N, RM>;
   if (done != nullptr && *done) return;
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(kThreads)
   T* sr = sm + (size_t)p * 2 * LS;
   T* si = sr + LS;
   T vr[F::R], vi[F::R];
-  const S* s0 = src + (size_t)row0 * N;
+  const SI* s0 = src + (size_t)row0 * N;
 #pragma unroll
   for (int q = 0; q < F::R; ++q) {
     vr[q] = valid ? to_compute<T>(s0[j + q * F::TS]) : T(0);
@@ -145,6 +149,91 @@ __global__ void __launch_bounds__(kThreads)
     o.x = to_storage<S>(h1 * scale);
     o.y = to_storage<S>(h2 * scale);
     *reinterpret_cast<V*>(data + base + (size_t)k * line_stride) = o;
+  }
+}
+
+// ------------------------------------ last axis, float-float, fused epilogue
+// The last 1D DHT (z in 3D, y in 2D) of FP64 lines in float-float
+// arithmetic; the transformed values h are not stored but consumed:
+//   EPI_THETA:  theta += h / mu            (theta = DHT(T_h v) accumulates)
+//   EPI_RESID:  out32 = h - theta (FP32), and sum of (h - theta)^2 into
+//               ctrl->res_l2 = (h^d / N sum)^{1/2} (Parseval)
+// with mu the symbol of -Delta_h at the element; the zero mode gives 0
+// (mean-zero projection).  Same thread mapping as k_dht_cols.
+enum { EPI_THETA = 0, EPI_RESID = 1 };
+template <int N, int RM, int EPI>
+__global__ void __launch_bounds__(kThreads)
+    k_dht_last_ff(const double* data, double* theta, float* out32, size_t line_stride, size_t outer_stride,
+                  KParams kp, Ctrl* ctrl, double* partials, const ff* __restrict__ twc,
+                  const ff* __restrict__ tws, const ff* __restrict__ symx, const ff* __restrict__ symo,
+                  const ff* __restrict__ syml) {
+  using T = ff;
+  using F = LineFFT<T, N, RM>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ float sred[32];
+  __shared__ int sflag;
+  const int tid = threadIdx.x;
+  const int pairs = blockDim.x / F::TS;
+  const int p = tid % pairs, j = tid / pairs;
+  const int x = blockIdx.x * 2 * pairs + 2 * p;
+  const size_t base = (size_t)blockIdx.y * outer_stride + x;
+  constexpr int LS = line_stride_words<T, N, RM, false>();
+  T* sr = sm + (size_t)p * 2 * LS;
+  T* si = sr + LS;
+  T vr[F::R], vi[F::R];
+#pragma unroll
+  for (int q = 0; q < F::R; ++q) {
+    const double2 v = *reinterpret_cast<const double2*>(data + base + (size_t)(j + q * F::TS) * line_stride);
+    vr[q] = to_compute<T>(v.x);
+    vi[q] = to_compute<T>(v.y);
+  }
+  F::run(vr, vi, j, sr, si, twc, tws);
+  const ff mo = symo != nullptr ? ld_tw(symo + blockIdx.y) : ff(0.0f, 0.0f);
+  const ff mx[2] = {ff_add(ld_tw(symx + x), mo), ff_add(ld_tw(symx + x + 1), mo)};
+  float acc = 0.0f;
+#pragma unroll
+  for (int q = 0; q < F::R; ++q) {
+    const int k = j + q * F::TS;
+    T h[2];
+    dht_split(sr, si, k, N, h[0], h[1]);
+    const ff ml = ld_tw(syml + k);
+    const size_t idx = base + (size_t)k * line_stride;
+    const double2 th = *reinterpret_cast<const double2*>(theta + idx);
+    const double thv[2] = {th.x, th.y};
+    double outv[2];
+    float o32[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const ff mu = ff_add(mx[c], ml);
+      const bool live = mu.hi > 0.0f;
+      if (EPI == EPI_THETA) {
+        const ff t = live ? ff_mul(h[c], ff_recip(mu)) : ff(0.0f, 0.0f);
+        outv[c] = ff_to_double_bits(ff_add(ff_from_double_bits(thv[c]), t));
+      } else {
+        const ff w = live ? ff_sub(h[c], ff_from_double_bits(thv[c])) : ff(0.0f, 0.0f);
+        o32[c] = w.hi;
+        acc = fmaf(w.hi, w.hi, acc);
+      }
+    }
+    if (EPI == EPI_THETA) {
+      *reinterpret_cast<double2*>(theta + idx) = make_double2(outv[0], outv[1]);
+    } else {
+      *reinterpret_cast<float2*>(out32 + idx) = make_float2(o32[0], o32[1]);
+    }
+  }
+  if (EPI == EPI_RESID) {
+    float v[1] = {acc};
+    block_reduce<float, 1, false>(v, sred);
+    if (publish_and_check_last<float>(v, 1, reinterpret_cast<float*>(partials), &ctrl->counter[CS_MID], &sflag)) {
+      float tt[1];
+      gather_partials<float, 1, false>(tt, reinterpret_cast<const float*>(partials), sred);
+      if (tid == 0) {
+        ctrl->res_l2 = sqrt((double)tt[0] * kp.hd * kp.inv_ntot);
+        ctrl->res_linf = -1.0;
+        ctrl->counter[CS_MID] = 0;
+      }
+    }
   }
 }
 
@@ -379,16 +468,16 @@ int pick_pairs(int avail_pairs) {
   return pairs < 1 ? 1 : pairs;
 }
 
-template <typename S, typename T, int N>
-cudaError_t rows_impl(const S* src, S* dst, int nrows, T scale, const int* done, const T* twc,
+template <typename S, typename T, int N, typename SI = S>
+cudaError_t rows_impl(const SI* src, S* dst, int nrows, T scale, const int* done, const T* twc,
                       const T* tws, cudaStream_t st) {
   constexpr int RM = radix_pass<T>();
   using F = LineFFT<T, N, RM>;
   const int pairs = pick_pairs<T, N, RM, true>(1 << 30);
   const int rows_per_block = 2 * pairs;
   const int grid = (nrows + rows_per_block - 1) / rows_per_block;
-  k_dht_rows<S, T, N, RM><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, true>(), st>>>(src, dst, nrows, scale,
-                                                                                  done, twc, tws);
+  k_dht_rows<S, T, N, RM, SI><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, true>(), st>>>(
+      src, dst, nrows, scale, done, twc, tws);
   return cudaGetLastError();
 }
 
@@ -454,7 +543,11 @@ void set_attrs() {
   cudaFuncSetAttribute(k_mid<T, N, 6, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   constexpr int RF = radix_pass<ff>();
   cudaFuncSetAttribute(k_dht_rows<double, ff, N, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_rows<double, ff, N, RF, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kMaxSmem);
   cudaFuncSetAttribute(k_dht_cols<double, ff, N, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_last_ff<N, RF, EPI_THETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_last_ff<N, RF, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
 }
 
 #define PSD_DISPATCH_N(n, CALL)      \
@@ -491,6 +584,44 @@ cudaError_t launch_dht_cols_ff(double* data, const KParams& kp, int ax, double s
   const int nouter = ax == 1 ? kp.nz : kp.ny;
   PSD_DISPATCH_N(n, (cols_impl<double, ff, NN>(data, kp.nx, nouter, line_stride, outer_stride, ff(scale), nullptr,
                                                tb.twc[ax], tb.tws[ax], st)));
+}
+
+cudaError_t launch_dht_rows_ff_from_f32(const float* src, double* dst, int nx, int nrows, const AxisTables<ff>& tb,
+                                        cudaStream_t st) {
+  PSD_DISPATCH_N(nx, (rows_impl<double, ff, NN, float>(src, dst, nrows, ff(1.0f, 0.0f), nullptr, tb.twc[0], tb.tws[0],
+                                                        st)));
+}
+
+template <int N>
+cudaError_t last_ff_impl(const double* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
+                         double* partials, const AxisTables<ff>& tb, cudaStream_t st) {
+  constexpr int RM = radix_pass<ff>();
+  using F = LineFFT<ff, N, RM>;
+  const int nx = kp.nx;
+  const int pairs = pick_pairs<ff, N, RM, false>(nx / 2);
+  const bool d3 = kp.dim == 3;
+  const size_t line_stride = d3 ? (size_t)nx * kp.ny : (size_t)nx;
+  const size_t outer_stride = d3 ? (size_t)nx : 0;
+  const int nouter = d3 ? kp.ny : 1;
+  const int ax = d3 ? 2 : 1;
+  dim3 grid(nx / (2 * pairs), nouter);
+  const size_t sm = pairs * pair_smem<ff, N, RM, false>();
+  const ff* symo = d3 ? tb.sym[1] : nullptr;
+  if (out32 == nullptr)
+    k_dht_last_ff<N, RM, EPI_THETA><<<grid, pairs * F::TS, sm, st>>>(data, theta, out32, line_stride, outer_stride,
+                                                                    kp, ctrl, partials, tb.twc[ax], tb.tws[ax],
+                                                                    tb.sym[0], symo, tb.sym[ax]);
+  else
+    k_dht_last_ff<N, RM, EPI_RESID><<<grid, pairs * F::TS, sm, st>>>(data, theta, out32, line_stride, outer_stride,
+                                                                    kp, ctrl, partials, tb.twc[ax], tb.tws[ax],
+                                                                    tb.sym[0], symo, tb.sym[ax]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dht_last_ff(const double* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
+                               double* partials, const AxisTables<ff>& tb, cudaStream_t st) {
+  const int n = kp.dim == 3 ? kp.nz : kp.ny;
+  PSD_DISPATCH_N(n, (last_ff_impl<NN>(data, theta, out32, kp, ctrl, partials, tb, st)));
 }
 
 template <typename T>

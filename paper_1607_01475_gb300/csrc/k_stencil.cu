@@ -755,19 +755,19 @@ cudaError_t res_impl(const ResArgs<T>& a, const KParams& kp, Ctrl* ctrl, double*
 template <typename T, int PK, bool INNER>
 cudaError_t ls_impl(const T* u, const T* ubase, const T* d, const KParams& kp, Ctrl* ctrl, double* partials,
                     cudaStream_t st) {
-  if (kp.dim == 3) {
-    const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY3 ? kp.ny : BY3;
-    const int gx = kp.nx / TX, gy = kp.ny / TY;
-    const int zc = pick_zc(kp.nz, gx * gy);
-    dim3 grid(gx, gy, kp.nz / zc);
-    if (kp.nx >= 32 && kp.ny >= 8)
-      k_ls3d_col<T, PK, INNER><<<grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, zc);
-    else
-      k_ls3d<T, PK, INNER><<<grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, zc);
-  } else {
-    const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY2 ? kp.ny : BY2;
-    dim3 grid(kp.nx / TX, kp.ny / TY);
-    k_ls2d<T, PK, INNER><<<grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials);
+  const ResGeom g = res_geometry(kp, sizeof(T) == 4);  // the same tiles as the residual
+  switch (g.kind) {
+    case RK_RB4:
+      if constexpr (sizeof(T) == 4) k_ls3d_rb<T, PK, INNER, 4><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, g.zc);
+      break;
+    case RK_COL:
+      k_ls3d_col<T, PK, INNER><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, g.zc);
+      break;
+    case RK_SMALL3D:
+      k_ls3d<T, PK, INNER><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, g.zc);
+      break;
+    default:
+      k_ls2d<T, PK, INNER><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials);
   }
   return cudaGetLastError();
 }

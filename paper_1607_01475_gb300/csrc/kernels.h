@@ -8,8 +8,7 @@
 
 namespace psd {
 
-// Per-axis tables owned by a context: FP64, FP32, and float-float twiddles
-// (no symbols).
+// Per-axis tables owned by a context, in FP64, FP32 and float-float.
 template <typename T>
 struct AxisTables {
   const T* twc[3];  // cos(2 pi t / n_a), t < n_a
@@ -35,6 +34,14 @@ cudaError_t launch_dht_rows_ff(const double* src, double* dst, int nx, int nrows
                                const AxisTables<ff>& tb, cudaStream_t st);
 cudaError_t launch_dht_cols_ff(double* data, const KParams& kp, int ax, double scale, const AxisTables<ff>& tb,
                                cudaStream_t st);
+// The x pass reading FP32 lines (writes FP64).
+cudaError_t launch_dht_rows_ff_from_f32(const float* src, double* dst, int nx, int nrows, const AxisTables<ff>& tb,
+                                        cudaStream_t st);
+// The last pass (z in 3D, y in 2D) with a fused epilogue: out32 == nullptr:
+// theta += DHT(data) / mu; else out32 = (float)(DHT(data) - theta) and
+// ctrl->res_l2 = its Parseval norm (h^d / N sum)^{1/2}.  mu = 0 gives 0.
+cudaError_t launch_dht_last_ff(const double* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
+                               double* partials, const AxisTables<ff>& tb, cudaStream_t st);
 
 // The middle pass along the slowest axis (y in 2D, z in 3D) of the
 // preconditioner: forward DHT, division by the symbol of L_h, Parseval sums

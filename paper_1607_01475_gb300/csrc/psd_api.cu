@@ -182,8 +182,16 @@ psd_status build_tables(psd_context* c) {
   std::vector<psd::ff> hff(tot);
   for (int a = 0; a < 3; ++a)
     for (int t = 0; t < n[a]; ++t)
-      for (int w = 0; w < 2; ++w) {
-        const long double v = w == 0 ? cosl(2.0L * pi * t / n[a]) : sinl(2.0L * pi * t / n[a]);
+      for (int w = 0; w < 3; ++w) {
+        long double v;
+        if (w == 0)
+          v = cosl(2.0L * pi * t / n[a]);
+        else if (w == 1)
+          v = sinl(2.0L * pi * t / n[a]);
+        else {
+          const long double sn = (n[a] > 1) ? sinl(pi * t / n[a]) : 0.0L;
+          v = 4.0L / (h * h) * sn * sn;
+        }
         const float hi = (float)v;
         hff[offs[a][w] + t] = psd::ff(hi, (float)(v - (long double)hi));
       }
@@ -203,7 +211,7 @@ psd_status build_tables(psd_context* c) {
     c->tb32.sym[a] = d32 + offs[a][2];
     c->tbff.twc[a] = dff + offs[a][0];
     c->tbff.tws[a] = dff + offs[a][1];
-    c->tbff.sym[a] = nullptr;
+    c->tbff.sym[a] = dff + offs[a][2];
   }
   return PSD_OK;
 }
@@ -310,6 +318,24 @@ psd_status full_dht_ff(psd_context* c, double* x, double scale) {
   return PSD_OK;
 }
 
+// theta += DHT(v) / mu (order 6, mixed): v is src64 (FP64, transformed in
+// place) or src32 (FP32, transformed into D); theta lives in Z.
+psd_status dht_theta_ff(psd_context* c, double* src64, const float* src32) {
+  const KParams& kp = c->kp;
+  const int nrows = kp.ny * kp.nz;
+  double* x = src32 ? c->D : src64;
+  if (src32) {
+    ProfScope p_(c, PSD_PROF_DHT_ROWS_FF);
+    CK(psd::launch_dht_rows_ff_from_f32(src32, x, kp.nx, nrows, c->tbff, c->st));
+  } else {
+    ProfScope p_(c, PSD_PROF_DHT_ROWS_FF);
+    CK(psd::launch_dht_rows_ff(x, x, kp.nx, nrows, 1.0, c->tbff, c->st));
+  }
+  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, 1.0, c->tbff, c->st)); }
+  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(x, c->Z, nullptr, kp, nullptr, c->partials, c->tbff, c->st)); }
+  return PSD_OK;
+}
+
 // The search-direction solve L_h d = W of one PSD iteration (W is consumed).
 template <typename T>
 psd_status precond_passes(psd_context* c, T* W, T* D, Ctrl* ctrl, T* xi, T* dspec, const AxisTables<T>& tb) {
@@ -378,8 +404,9 @@ psd_status residual64(psd_context* c, const double* u, const double* f, const do
 }
 
 // Sixth-order outer residual in the transform domain (mixed precision):
-// W <- DHT(P0[f - N_h^{loc}[u]] - T_h[u - g]) using zeta64 = DHT(u - g) in Z;
-// ||R||_2 by Parseval into *res.
+// R32 <- (float) DHT(P0[f - N_h^{loc}[u]] - T_h[u - g]) = DHT(r_loc) - theta
+// with theta = DHT(T_h[u - g]) in Z (the subtraction, the rounding and the
+// Parseval norm fused into the last transform pass); ||R||_2 into *res.
 psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f, double* res) {
   const KParams& kp = c->kp;
   Ctrl h;
@@ -387,9 +414,10 @@ psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f
   TRY(upload_ctrl(c, c->ctrl2, h));
   ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
-  TRY(full_dht_ff(c, c->W, 1.0));
-  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec6_combine<double>(c->W, c->Z, kp, c->tb64, c->st)); }
-  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(c->W, c->N, kp.hd * kp.inv_ntot, c->ctrl2, c->partials, c->st)); }
+  const int nrows = kp.ny * kp.nz;
+  { ProfScope p_(c, PSD_PROF_DHT_ROWS_FF); CK(psd::launch_dht_rows_ff(c->W, c->W, kp.nx, nrows, 1.0, c->tbff, c->st)); }
+  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(c->W, kp, 1, 1.0, c->tbff, c->st)); }
+  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(c->W, c->Z, c->R32, kp, c->ctrl2, c->partials, c->tbff, c->st)); }
   Ctrl h2;
   TRY(read_ctrl(c, c->ctrl2, h2));
   *res = h2.res_l2;
@@ -474,9 +502,10 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
   }
   { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
   if (six) {
-    // zeta64 = DHT(u0 - g), advanced with DHT(delta) after every correction
-    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
-    TRY(full_dht_ff(c, c->Z, 1.0));
+    // theta = DHT(T_h[u0 - g]), advanced with DHT(T_h delta) after every correction
+    CK(cudaMemsetAsync(c->Z, 0, c->N * sizeof(double), c->st));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->D, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
+    TRY(dht_theta_ff(c, c->D, nullptr));
   }
   int inner_total = 0, outer = 0;
   int status = PSD_ERR_NOCONV;
@@ -486,10 +515,7 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
     if (delta) {
       { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, delta, c->u32, c->N, c->st)); }
       if (six) {
-        // zeta64 += DHT(delta)
-        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_widen_f64(c->D, delta, c->N, c->st)); }
-        TRY(full_dht_ff(c, c->D, 1.0));
-        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, c->Z, c->D, 1.0, 1.0, 0.0, c->N, c->st)); }
+        TRY(dht_theta_ff(c, nullptr, delta));  // theta += DHT(T_h delta)
         // keep mean(u) = mean(g) exactly: delta is mean-zero only up to FP32 rounding
         Ctrl hu;
         { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
@@ -512,7 +538,7 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
       resinf = h2.res_linf;
     }
     ++outer;
-    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->R32, c->W, c->N, c->st)); }
+    if (!six) { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->R32, c->W, c->N, c->st)); }
     if (!std::isfinite(res)) {
       status = PSD_ERR_NONFINITE;
       break;

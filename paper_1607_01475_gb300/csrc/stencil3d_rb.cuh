@@ -472,5 +472,131 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
+// Register-blocked 3D line-search reduction (tiles of 32 x 8*NY vertices).
+// Vertex (cy, cx) of the tile sits at (y0 + cy + 1/2, x0 + cx + 1/2); each
+// thread owns the vertices of NY consecutive rows of one column.  The z-pair
+// sums / differences of u (+ base) and d of its own cells are formed in
+// registers; those of the cells at x + 1 and of the row below the strip come
+// through shared memory (double-buffered, one barrier per plane).  The extra
+// column (x0 + 32) and row (y0 + 8 NY) of cells are carried by threads
+// tid < 8 NY + 33.  Same unscaled vertex sums as the column kernel.
+template <typename T, int PK, bool INNER, int NY>
+__global__ void __launch_bounds__(256, 3)
+    k_ls3d_rb(const T* __restrict__ u, const T* __restrict__ ubase, const T* __restrict__ d, KParams kp,
+              Ctrl* ctrl, double* partials, int zc) {
+  if (ctrl->done) return;
+  if (PK != PK_4 && ctrl->c3 != 0.0) return;  // Newton already converged
+  constexpr int TX = 32, TYT = 8 * NY;
+  constexpr int SX = TX + 1, SY = TYT + 1;  // cells x0 .. x0+TX, y0 .. y0+TYT
+  constexpr int NH = SY + TX;               // halo cells: column TX (SY) and row TYT (TX)
+  __shared__ T sPu[2][SY][SX], sMu[2][SY][SX], sPd[2][SY][SX], sMd[2][SY][SX];
+  __shared__ T sred[32 * 3];
+  __shared__ int sflag;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TYT, z0 = blockIdx.z * zc;
+  const size_t plane = (size_t)nx * ny;
+  const T beta = kconst<T>(kp).beta, pm2 = kconst<T>(kp).pm2;
+  const T trial = (PK == PK_4) ? T(0) : (T)ctrl->alpha;
+  const int cy0 = ty * NY;
+  const int ooff0 = (y0 + cy0) * nx + x0 + tx;  // own cell of row i: ooff0 + i nx
+  const bool hv = tid < NH;
+  const int hly = tid < SY ? tid : TYT, hlx = tid < SY ? TX : tid - SY;
+  const int hoff = ((y0 + hly) & (ny - 1)) * nx + ((x0 + hlx) & (nx - 1));
+
+  T pu[NY], pd[NY], hu[NY], hd[NY], Pu[NY], Mu[NY], Pd[NY], Md[NY];
+  T puh = T(0), pdh = T(0), huh = T(0), hdh = T(0);
+#pragma unroll
+  for (int i = 0; i < NY; ++i) pu[i] = pd[i] = hu[i] = hd[i] = Pu[i] = Mu[i] = Pd[i] = Md[i] = T(0);
+  auto fetch = [&](int zz) {
+    const size_t gz = (size_t)(zz & (nz - 1)) * plane;
+#pragma unroll
+    for (int i = 0; i < NY; ++i) {
+      const size_t g = gz + ooff0 + (size_t)i * nx;
+      T v = u[g];
+      if (INNER) v += ubase[g];
+      pu[i] = v;
+      pd[i] = d[g];
+    }
+    if (hv) {
+      T v = u[gz + hoff];
+      if (INNER) v += ubase[gz + hoff];
+      puh = v;
+      pdh = d[gz + hoff];
+    }
+  };
+  // P/M of the vertex plane between the history and the fetched plane
+  auto store = [&](int buf, bool first) {
+#pragma unroll
+    for (int i = 0; i < NY; ++i) {
+      if (!first) {
+        Pu[i] = hu[i] + pu[i];
+        Mu[i] = pu[i] - hu[i];
+        Pd[i] = hd[i] + pd[i];
+        Md[i] = pd[i] - hd[i];
+        sPu[buf][cy0 + i][tx] = Pu[i];
+        sMu[buf][cy0 + i][tx] = Mu[i];
+        sPd[buf][cy0 + i][tx] = Pd[i];
+        sMd[buf][cy0 + i][tx] = Md[i];
+      }
+      hu[i] = pu[i];
+      hd[i] = pd[i];
+    }
+    if (hv) {
+      if (!first) {
+        sPu[buf][hly][hlx] = huh + puh;
+        sMu[buf][hly][hlx] = puh - huh;
+        sPd[buf][hly][hlx] = hdh + pdh;
+        sMd[buf][hly][hlx] = pdh - hdh;
+      }
+      huh = puh;
+      hdh = pdh;
+    }
+  };
+  T acc[3] = {T(0), T(0), T(0)};
+  fetch(z0);
+  store(0, true);
+  fetch(z0 + 1);
+  for (int z = z0; z < z0 + zc; ++z) {
+    const int buf = (z - z0) & 1;
+    store(buf, false);  // vertex plane z + 1/2
+    __syncthreads();
+    fetch(z + 2);
+    T xPu[NY + 1], xMu[NY + 1], xPd[NY + 1], xMd[NY + 1];  // cells (cy0 + i, tx + 1)
+#pragma unroll
+    for (int i = 0; i <= NY; ++i) {
+      xPu[i] = sPu[buf][cy0 + i][tx + 1];
+      xMu[i] = sMu[buf][cy0 + i][tx + 1];
+      xPd[i] = sPd[buf][cy0 + i][tx + 1];
+      xMd[i] = sMd[buf][cy0 + i][tx + 1];
+    }
+    const T nPu = sPu[buf][cy0 + NY][tx], nMu = sMu[buf][cy0 + NY][tx];  // cell (cy0 + NY, tx)
+    const T nPd = sPd[buf][cy0 + NY][tx], nMd = sMd[buf][cy0 + NY][tx];
+#pragma unroll
+    for (int i = 0; i < NY; ++i) {
+      const T p10 = i == NY - 1 ? nPu : Pu[i + 1], m10 = i == NY - 1 ? nMu : Mu[i + 1];
+      const T q10 = i == NY - 1 ? nPd : Pd[i + 1], n10 = i == NY - 1 ? nMd : Md[i + 1];
+      T av[3], bv[3];
+      av[0] = (xPu[i] - Pu[i]) + (xPu[i + 1] - p10);
+      av[1] = (p10 - Pu[i]) + (xPu[i + 1] - xPu[i]);
+      av[2] = (Mu[i] + xMu[i]) + (m10 + xMu[i + 1]);
+      bv[0] = (xPd[i] - Pd[i]) + (xPd[i + 1] - q10);
+      bv[1] = (q10 - Pd[i]) + (xPd[i + 1] - xPd[i]);
+      bv[2] = (Md[i] + xMd[i]) + (n10 + xMd[i + 1]);
+      ls_accumulate<PK>(av, bv, trial, beta, pm2, acc);
+    }
+  }
+  T v[3] = {acc[0], acc[1], acc[2]};
+  block_reduce<T, 3, false>(v, sred);
+  if (publish_and_check_last<T>(v, 3, reinterpret_cast<T*>(partials), &ctrl->counter[CS_LS], &sflag)) {
+    T tt[3];
+    gather_partials<T, 3, false>(tt, reinterpret_cast<const T*>(partials), sred);
+    if (tid == 0) {
+      const double tot[3] = {(double)tt[0], (double)tt[1], (double)tt[2]};
+      linesearch_epilogue<PK>(ctrl, kp, tot);
+    }
+  }
+}
+
 }  // namespace
 }  // namespace psd
