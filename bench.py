@@ -106,7 +106,7 @@ class ClockSampler:
 # Algorithmic bytes per cell per launch of each kernel class on the
 # sixth-order path (reads + writes of whole fields, in the class precision).
 def algorithmic_bytes_per_cell(cls, order):
-    w = 8 if cls.endswith("fp64") else 4
+    w = 8 if cls.endswith("fp64") or cls.endswith("_ff") else 4  # float-float passes keep FP64 storage
     fp32 = cls.endswith("fp32")
     table = {
         # inner (order 6): delta, d, ubase in; delta', r out.  FP64 plain: u, d, f in; u', r out
@@ -335,6 +335,7 @@ def run_gpu(args):
             "res_l2": infos_mixed[-1]["res_l2"],
             "speedup_time_to_tol_mixed_vs_fp64": (ms64 / steps64) / (ms_mixed / args.steps),
             "roofline": roof, "kernel_time_share_mixed": share,
+            "kernel_ms_per_solve_mixed": {k: round(v[0] / args.steps, 3) for k, v in prof.items() if v[1]},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": total_launches, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)

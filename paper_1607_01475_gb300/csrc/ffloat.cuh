@@ -15,7 +15,8 @@
 //                 arithmetic", ACM TOMS 44(2), 2017: relative errors of a
 //                 few u^2 (u = 2^-24);
 //   ff_mul_f      a double-word times an FP32 number exactly representable
-//                 in it (as DWTimesFP with FMA from the same paper).
+//                 in it (as DWTimesFP with FMA from the same paper);
+//   ff_add_fast   "SloppyDWPlusDW" of the same paper, for FFT butterflies.
 // The compiler must not reassociate these: the build uses no fast-math.
 #pragma once
 
@@ -91,6 +92,22 @@ __host__ __device__ __forceinline__ ff ff_add(ff x, ff y) {
 
 __host__ __device__ __forceinline__ ff ff_neg(ff x) { return ff(-x.hi, -x.lo); }
 __host__ __device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+
+// The cheaper double-word sum ("SloppyDWPlusDW" of the same paper: 11
+// operations).  Its error is below a few u^2 (|x| + |y|) in absolute terms
+// but not relative to a sum that cancels; that is the bound the error
+// analysis of an FFT butterfly needs (its error is measured against the
+// norm of the data), so the line FFT uses it.  Where the cancellation is
+// the point (a residual as the difference of two nearly equal transforms)
+// ff_add is used.
+__host__ __device__ __forceinline__ ff ff_add_fast(ff x, ff y) {
+  float sh, sl;
+  two_sum(x.hi, y.hi, sh, sl);
+  const float v = f_add(sl, f_add(x.lo, y.lo));
+  ff z;
+  fast_two_sum(sh, v, z.hi, z.lo);
+  return z;
+}
 
 __host__ __device__ __forceinline__ ff ff_mul(ff x, ff y) {
   const float ch = f_mul(x.hi, y.hi);
@@ -237,9 +254,10 @@ __host__ __device__ __forceinline__ double ff_to_double_bits(ff x) {
   return ff_bitsd(sgn | ((unsigned long long)(e + 1023) << 52) | ((unsigned long long)n & 0xFFFFFFFFFFFFFULL));
 }
 
-// Arithmetic operators so that the line-FFT templates run on ff.
-__host__ __device__ __forceinline__ ff operator+(ff a, ff b) { return ff_add(a, b); }
-__host__ __device__ __forceinline__ ff operator-(ff a, ff b) { return ff_sub(a, b); }
+// Arithmetic operators so that the line-FFT templates run on ff (sums with
+// the butterfly-grade ff_add_fast).
+__host__ __device__ __forceinline__ ff operator+(ff a, ff b) { return ff_add_fast(a, b); }
+__host__ __device__ __forceinline__ ff operator-(ff a, ff b) { return ff_add_fast(a, ff_neg(b)); }
 __host__ __device__ __forceinline__ ff operator-(ff a) { return ff_neg(a); }
 __host__ __device__ __forceinline__ ff operator*(ff a, ff b) { return ff_mul(a, b); }
 

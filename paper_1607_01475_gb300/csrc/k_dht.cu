@@ -71,7 +71,11 @@ __host__ __device__ constexpr int line_stride_words() {
   }
   return L + (((r - L) % M) + M) % M;
 }
-constexpr size_t kMaxSmem = 96 * 1024;
+constexpr size_t kMaxSmem = 96 * 1024;       // line-pair buffers of a block
+constexpr size_t kMaxSmemPre = 200 * 1024;   // with the prefetch buffers of the last-axis passes
+
+// Bytes of the line-pair region rounded up to 16 (the prefetch region follows).
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // -------------------------------------------------------------- x (rows)
 // S: element type in memory (SI of the source); T: arithmetic type.
@@ -181,14 +185,20 @@ __global__ void __launch_bounds__(kThreads)
   constexpr int LS = line_stride_words<T, N, RM, false>();
   T* sr = sm + (size_t)p * 2 * LS;
   T* si = sr + LS;
+  // theta of this thread's elements, copied asynchronously while the
+  // forward transform runs: [q][j][p] double2
+  double2* pre = reinterpret_cast<double2*>(smem_raw + align16((size_t)pairs * 2 * LS * sizeof(T)));
   T vr[F::R], vi[F::R];
 #pragma unroll
   for (int q = 0; q < F::R; ++q) {
-    const double2 v = *reinterpret_cast<const double2*>(data + base + (size_t)(j + q * F::TS) * line_stride);
+    const size_t idx = base + (size_t)(j + q * F::TS) * line_stride;
+    const double2 v = *reinterpret_cast<const double2*>(data + idx);
+    cp_async_16(pre + ((size_t)(q * F::TS + j) * pairs + p), theta + idx);
     vr[q] = to_compute<T>(v.x);
     vi[q] = to_compute<T>(v.y);
   }
   F::run(vr, vi, j, sr, si, twc, tws);
+  cp_async_wait_all();
   const ff mo = symo != nullptr ? ld_tw(symo + blockIdx.y) : ff(0.0f, 0.0f);
   const ff mx[2] = {ff_add(ld_tw(symx + x), mo), ff_add(ld_tw(symx + x + 1), mo)};
   float acc = 0.0f;
@@ -199,7 +209,7 @@ __global__ void __launch_bounds__(kThreads)
     dht_split(sr, si, k, N, h[0], h[1]);
     const ff ml = ld_tw(syml + k);
     const size_t idx = base + (size_t)k * line_stride;
-    const double2 th = *reinterpret_cast<const double2*>(theta + idx);
+    const double2 th = pre[(size_t)(q * F::TS + j) * pairs + p];
     const double thv[2] = {th.x, th.y};
     double outv[2];
     float o32[2];
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(kThreads)
 
 // ------------------------------------------------------------- middle pass
 template <typename T, int N, int ORDER, int RM>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 && ORDER == 4 ? 3 : 2)
     k_mid(T* data, size_t line_stride, size_t outer_stride, KParams kp, Ctrl* ctrl, double* partials,
           T* xi, T* dspec, const T* __restrict__ symx, const T* __restrict__ symo,
           const T* __restrict__ syml, const T* __restrict__ twc, const T* __restrict__ tws) {
@@ -258,14 +268,30 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
   constexpr int LS = line_stride_words<T, N, RM, false>();
   T* sr = sm + (size_t)p * 2 * LS;
   T* si = sr + LS;
+  // order 6: xi and dspec of this thread's elements, copied asynchronously
+  // while the forward transform runs ([q][j][p] pairs of columns)
+  V* pre_x = reinterpret_cast<V*>(smem_raw + align16((size_t)pairs * 2 * LS * sizeof(T)));
+  V* pre_d = pre_x + (size_t)N * pairs;
   T vr[F::R], vi[F::R];
 #pragma unroll
   for (int q = 0; q < F::R; ++q) {
-    const V v = *reinterpret_cast<const V*>(data + base + (size_t)(j + q * F::TS) * line_stride);
+    const size_t idx = base + (size_t)(j + q * F::TS) * line_stride;
+    const V v = *reinterpret_cast<const V*>(data + idx);
+    if (ORDER == 6) {
+      const size_t e = (size_t)(q * F::TS + j) * pairs + p;
+      if (sizeof(V) == 8) {
+        cp_async_8(pre_x + e, xi + idx);
+        cp_async_8(pre_d + e, dspec + idx);
+      } else {
+        cp_async_16(pre_x + e, xi + idx);
+        cp_async_16(pre_d + e, dspec + idx);
+      }
+    }
     vr[q] = v.x;
     vi[q] = v.y;
   }
   F::run(vr, vi, j, sr, si, twc, tws);
+  if (ORDER == 6) cp_async_wait_all();
 
   const T mo = (symo != nullptr) ? symo[blockIdx.y] : T(0);
   const T mxa = symx[x] + mo, mxb = symx[x + 1] + mo;
@@ -299,8 +325,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
       // d = rt / L = mu rt / P and T_h d = d / mu = rt / P, where
       // P = 1 + mu (lam s + mu (s + s eps^2 mu)) >= 1: one reciprocal.
       const size_t idx = base + (size_t)k * line_stride;
-      const V xv = *reinterpret_cast<const V*>(xi + idx);
-      const V dp = *reinterpret_cast<const V*>(dspec + idx);
+      const V xv = pre_x[(size_t)(q * F::TS + j) * pairs + p];
+      const V dp = pre_d[(size_t)(q * F::TS + j) * pairs + p];
       const T xs[2] = {xv.x, xv.y}, ds[2] = {dp.x, dp.y};
       T xn[2], tn[2];
 #pragma unroll
@@ -524,7 +550,10 @@ cudaError_t mid_impl(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T
     tws = tb.tws[2];
   }
   dim3 grid(nx / (2 * pairs), nouter);
-  const size_t sm = pairs * pair_smem<T, N, RM, false>();
+  using V = typename Vec2<T>::type;
+  const size_t sm = kp.order == 6 ? align16(pairs * pair_smem<T, N, RM, false>()) + 2 * (size_t)N * pairs * sizeof(V)
+                                  : pairs * pair_smem<T, N, RM, false>();
+  if (sm > kMaxSmemPre) return cudaErrorInvalidConfiguration;
   if (kp.order == 4)
     k_mid<T, N, 4, RM><<<grid, pairs * F::TS, sm, st>>>(data, line_stride, outer_stride, kp, ctrl, partials,
                                                    xi, dspec, tb.sym[0], symo, syml, twc, tws);
@@ -540,14 +569,16 @@ void set_attrs() {
   cudaFuncSetAttribute(k_dht_rows<T, T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   cudaFuncSetAttribute(k_dht_cols<T, T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   cudaFuncSetAttribute(k_mid<T, N, 4, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_mid<T, N, 6, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_mid<T, N, 6, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPre);
   constexpr int RF = radix_pass<ff>();
   cudaFuncSetAttribute(k_dht_rows<double, ff, N, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   cudaFuncSetAttribute(k_dht_rows<double, ff, N, RF, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kMaxSmem);
   cudaFuncSetAttribute(k_dht_cols<double, ff, N, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_dht_last_ff<N, RF, EPI_THETA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_dht_last_ff<N, RF, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_last_ff<N, RF, EPI_THETA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kMaxSmemPre);
+  cudaFuncSetAttribute(k_dht_last_ff<N, RF, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kMaxSmemPre);
 }
 
 #define PSD_DISPATCH_N(n, CALL)      \
@@ -605,7 +636,8 @@ cudaError_t last_ff_impl(const double* data, double* theta, float* out32, const 
   const int nouter = d3 ? kp.ny : 1;
   const int ax = d3 ? 2 : 1;
   dim3 grid(nx / (2 * pairs), nouter);
-  const size_t sm = pairs * pair_smem<ff, N, RM, false>();
+  const size_t sm = align16(pairs * pair_smem<ff, N, RM, false>()) + (size_t)N * pairs * sizeof(double2);
+  if (sm > kMaxSmemPre) return cudaErrorInvalidConfiguration;
   const ff* symo = d3 ? tb.sym[1] : nullptr;
   if (out32 == nullptr)
     k_dht_last_ff<N, RM, EPI_THETA><<<grid, pairs * F::TS, sm, st>>>(data, theta, out32, line_stride, outer_stride,

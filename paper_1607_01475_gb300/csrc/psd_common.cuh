@@ -225,6 +225,19 @@ __device__ __forceinline__ int wrapi(int i, int n) {  // n a power of two
   return i & (n - 1);
 }
 
+// Asynchronous global -> shared copies (cp.async, 8 or 16 bytes, both
+// addresses aligned to the size); a thread that reads back only its own
+// copies needs cp_async_wait_all() and no barrier.
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // 1/x for finite x >= 1 (the preconditioner symbols).  FP32: the hardware
 // reciprocal estimate (rcp.approx) refined by one Newton-Raphson step
 // r <- r + r (1 - x r), which squares the estimate's relative error, so the

@@ -345,19 +345,23 @@ __global__ void __launch_bounds__(256, 3)
     const int ly = e / SX, lx = e - ly * SX;
     off[k] = ((y0 + ly) & (ny - 1)) * nx + ((x0 + lx) & (nx - 1));
   }
-  T pu[2] = {T(0), T(0)}, pdv[2] = {T(0), T(0)}, hu[2] = {T(0), T(0)}, hdd[2] = {T(0), T(0)};
+  // prefetched plane: u, base and d kept apart until used a step later
+  T pu[2] = {T(0), T(0)}, pbv[2] = {T(0), T(0)}, pdv[2] = {T(0), T(0)}, hu[2] = {T(0), T(0)},
+    hdd[2] = {T(0), T(0)};
   auto fetch = [&](int zz) {
     const size_t gz = (size_t)(zz & (nz - 1)) * plane;
 #pragma unroll
     for (int k = 0; k < 2; ++k)
       if (val[k]) {
-        T vv = u[gz + off[k]];
-        if (INNER) vv += ubase[gz + off[k]];
-        pu[k] = vv;
+        pu[k] = u[gz + off[k]];
+        if (INNER) pbv[k] = ubase[gz + off[k]];
         pdv[k] = d[gz + off[k]];
       }
   };
   auto store = [&](int buf, bool first) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (val[k] && INNER) pu[k] += pbv[k];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
       if (val[k]) {

@@ -504,29 +504,34 @@ __global__ void __launch_bounds__(256, 3)
   const int hly = tid < SY ? tid : TYT, hlx = tid < SY ? TX : tid - SY;
   const int hoff = ((y0 + hly) & (ny - 1)) * nx + ((x0 + hlx) & (nx - 1));
 
-  T pu[NY], pd[NY], hu[NY], hd[NY], Pu[NY], Mu[NY], Pd[NY], Md[NY];
-  T puh = T(0), pdh = T(0), huh = T(0), hdh = T(0);
+  // prefetched plane: u, base and d kept apart until the plane is used a
+  // step later (summing them at fetch time would wait on the loads there)
+  T pu[NY], pb[NY], pd[NY], hu[NY], hd[NY], Pu[NY], Mu[NY], Pd[NY], Md[NY];
+  T puh = T(0), pbh = T(0), pdh = T(0), huh = T(0), hdh = T(0);
 #pragma unroll
-  for (int i = 0; i < NY; ++i) pu[i] = pd[i] = hu[i] = hd[i] = Pu[i] = Mu[i] = Pd[i] = Md[i] = T(0);
+  for (int i = 0; i < NY; ++i) pu[i] = pb[i] = pd[i] = hu[i] = hd[i] = Pu[i] = Mu[i] = Pd[i] = Md[i] = T(0);
   auto fetch = [&](int zz) {
     const size_t gz = (size_t)(zz & (nz - 1)) * plane;
 #pragma unroll
     for (int i = 0; i < NY; ++i) {
       const size_t g = gz + ooff0 + (size_t)i * nx;
-      T v = u[g];
-      if (INNER) v += ubase[g];
-      pu[i] = v;
+      pu[i] = u[g];
+      if (INNER) pb[i] = ubase[g];
       pd[i] = d[g];
     }
     if (hv) {
-      T v = u[gz + hoff];
-      if (INNER) v += ubase[gz + hoff];
-      puh = v;
+      puh = u[gz + hoff];
+      if (INNER) pbh = ubase[gz + hoff];
       pdh = d[gz + hoff];
     }
   };
   // P/M of the vertex plane between the history and the fetched plane
   auto store = [&](int buf, bool first) {
+    if (INNER) {
+#pragma unroll
+      for (int i = 0; i < NY; ++i) pu[i] += pb[i];
+      puh += pbh;
+    }
 #pragma unroll
     for (int i = 0; i < NY; ++i) {
       if (!first) {

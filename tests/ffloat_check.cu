@@ -35,7 +35,7 @@ static bool normalised(ff x) {
 
 int main() {
   int fails = 0;
-  double worst_rt = 0, worst_split = 0, worst_add = 0, worst_mul = 0, worst_back = 0, worst_rcp = 0;
+  double worst_rt = 0, worst_split = 0, worst_add = 0, worst_mul = 0, worst_back = 0, worst_rcp = 0, worst_fast = 0;
   for (int t = 0; t < 200000; ++t) {
     const double v = rand_double(-100, 100);
     const ff a = psd::ff_from_double_bits(v);
@@ -61,6 +61,15 @@ int main() {
     const double rp = (double)(std::fabs(exact(p) - ep) / std::fabs(ep));
     if (rp > worst_mul) worst_mul = rp;
     if (!normalised(s) || !normalised(p)) ++fails;
+    // the butterfly sum: absolute error within a few u^2 (|b| + |c|), also under cancellation
+    {
+      const ff cc = (t & 1) ? psd::ff_neg(psd::ff_add(b, psd::ff_from_double_bits(rand_double(-60, -40)))) : c;
+      const ff q = psd::ff_add_fast(b, cc);
+      const long double eq = exact(b) + exact(cc);
+      const double r = (double)(std::fabs(exact(q) - eq) / (std::fabs(exact(b)) + std::fabs(exact(cc))));
+      if (r > worst_fast) worst_fast = r;
+      if (!normalised(q)) ++fails;
+    }
     // reciprocal of a positive double-word (the symbols of -Delta_h)
     const ff m = psd::ff_from_double_bits(std::fabs(rand_double(-20, 20)));
     const ff rm = psd::ff_recip(m);
@@ -85,8 +94,9 @@ int main() {
   if (worst_split > 0x1p-47 || worst_rt > 0x1p-47 || worst_back > 0x1p-52 || worst_add > 4 * u2 ||
       worst_mul > 6 * u2)
     ++fails;
-  std::printf("recip %.3g (%.2f units of 2^-48)\n", worst_rcp, worst_rcp / u2);
-  if (worst_rcp > 8 * u2) ++fails;
+  std::printf("recip %.3g (%.2f units of 2^-48)  fast sum %.3g (%.2f units of 2^-48, normwise)\n", worst_rcp,
+              worst_rcp / u2, worst_fast, worst_fast / u2);
+  if (worst_rcp > 8 * u2 || worst_fast > 4 * u2) ++fails;
   std::printf("%s (%d failures)\n", fails ? "FAIL" : "OK", fails);
   return fails ? 1 : 0;
 }
