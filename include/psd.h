@@ -69,6 +69,11 @@ typedef struct psd_params {
   int max_iter;     /* PSD iterations (mixed: total inner iterations)         */
   int max_outer;    /* mixed mode: outer FP64 residual corrections             */
   void* stream;     /* cudaStream_t                                            */
+  double inner_eta; /* mixed mode: an inner FP32 solve stops when its
+                       preconditioned norm (r, L_h^{-1} r)^{1/2} has dropped by
+                       this factor; 0 = default (1e-4); in [0, 1)               */
+  int inner_stall;  /* ... or when that norm has not halved in this many
+                       iterations (its FP32 floor); 0 = default (5)            */
 } psd_params;
 
 typedef struct psd_info {

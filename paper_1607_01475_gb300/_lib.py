@@ -25,7 +25,7 @@ class PSDParams(ctypes.Structure):
                 ("h", ctypes.c_double), ("p", ctypes.c_double), ("s", ctypes.c_double),
                 ("eps", ctypes.c_double), ("lam", ctypes.c_double), ("precision", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("inner_eta", ctypes.c_double), ("inner_stall", ctypes.c_int)]
 
 
 class PSDInfo(ctypes.Structure):
@@ -132,14 +132,15 @@ def _stream_handle(stream):
 # ------------------------------------------------------------ C-named calls
 
 def psd_create(order, shape, h, p, s, eps, lam=0.0, precision=PSD_FP64, tol=1e-10,
-               max_iter=10000, max_outer=20, stream=None):
+               max_iter=10000, max_outer=20, stream=None, inner_eta=0.0, inner_stall=0):
     """Create a solver handle for a grid of ``shape`` ((ny, nx) or (nz, ny, nx))."""
     lib = load_library()
     dim = len(shape)
     n = (shape[-1], shape[-2], shape[0] if dim == 3 else 1)
     prm = PSDParams(order=order, dim=dim, n=(ctypes.c_int * 3)(*n), h=h, p=p, s=s, eps=eps, lam=lam,
                     precision=precision, tol=tol, max_iter=max_iter, max_outer=max_outer,
-                    stream=_stream_handle(stream) if stream is not False else None)
+                    stream=_stream_handle(stream) if stream is not False else None,
+                    inner_eta=inner_eta, inner_stall=inner_stall)
     out = ctypes.c_void_p()
     _check(lib.psd_create(ctypes.byref(prm), ctypes.byref(out)), None)
     return out
@@ -208,11 +209,12 @@ def psd_residual_noalloc(shape, h, p, s, eps, u, f, r, stream=None):
 
 
 def _params(order, shape, h, p, s, eps, lam=0.0, precision=PSD_FP64, tol=1e-10, max_iter=10000,
-            max_outer=20, stream=None):
+            max_outer=20, stream=None, inner_eta=0.0, inner_stall=0):
     dim = len(shape)
     n = (shape[-1], shape[-2], shape[0] if dim == 3 else 1)
     return PSDParams(order=order, dim=dim, n=(ctypes.c_int * 3)(*n), h=h, p=p, s=s, eps=eps, lam=lam,
-                     precision=precision, tol=tol, max_iter=max_iter, max_outer=max_outer, stream=stream)
+                     precision=precision, tol=tol, max_iter=max_iter, max_outer=max_outer, stream=stream,
+                     inner_eta=inner_eta, inner_stall=inner_stall)
 
 
 class Batch:
@@ -264,10 +266,10 @@ class Solver:
     """Owns one handle.  ``shape`` is (ny, nx) or (nz, ny, nx)."""
 
     def __init__(self, order, shape, h, p, s, eps, lam=0.0, precision=PSD_FP64, tol=1e-10,
-                 max_iter=10000, max_outer=20, stream=None):
+                 max_iter=10000, max_outer=20, stream=None, inner_eta=0.0, inner_stall=0):
         self.shape = tuple(shape)
         self.handle = psd_create(order, shape, h, p, s, eps, lam, precision, tol, max_iter,
-                                 max_outer, stream)
+                                 max_outer, stream, inner_eta, inner_stall)
         self._hist = None
 
     def close(self):

@@ -148,6 +148,8 @@ psd_status validate(const psd_params* p, std::string& why) {
   if (!(p->tol >= 0) || !std::isfinite(p->tol)) return why = "tol must be >= 0", PSD_ERR_INVALID;
   if (p->max_iter < 0) return why = "max_iter must be >= 0", PSD_ERR_INVALID;
   if (p->precision == PSD_MIXED && p->max_outer < 1) return why = "max_outer must be >= 1", PSD_ERR_INVALID;
+  if (!(p->inner_eta >= 0 && p->inner_eta < 1)) return why = "inner_eta must be in [0, 1)", PSD_ERR_INVALID;
+  if (p->inner_stall < 0) return why = "inner_stall must be >= 0", PSD_ERR_INVALID;
   return PSD_OK;
 }
 
@@ -559,8 +561,8 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
     // kInnerEta, or when it has stopped halving (its FP32 floor).
     Ctrl h;
     init_ctrl(h, 0.0, std::min(c->prm.max_iter - inner_total, kInnerMaxIter));
-    h.pre_eta = kInnerEta;
-    h.pre_stall_max = kInnerStall;
+    h.pre_eta = c->prm.inner_eta > 0.0 ? c->prm.inner_eta : kInnerEta;
+    h.pre_stall_max = c->prm.inner_stall > 0 ? c->prm.inner_stall : kInnerStall;
     TRY(upload_ctrl(c, c->ctrl, h));
     CK(cudaMemsetAsync(c->da, 0, c->N * sizeof(float), c->st));
     if (six) CK(cudaMemsetAsync(c->Dsp32, 0, c->N * sizeof(float), c->st));

@@ -55,7 +55,7 @@ def _params(**kw):
     dict(n=(ctypes.c_int * 3)(64, 64, 2)), dict(h=0.0), dict(h=float("nan")), dict(p=1.5),
     dict(dim=3, n=(ctypes.c_int * 3)(8, 8, 8), p=7.0), dict(s=-1.0), dict(eps=0.0),
     dict(lam=-1.0), dict(precision=3), dict(tol=-1.0), dict(max_iter=-1),
-    dict(precision=1, max_outer=0),
+    dict(precision=1, max_outer=0), dict(inner_eta=1.0), dict(inner_eta=-0.5), dict(inner_stall=-1),
 ])
 def test_create_rejects_invalid_parameters(lib, bad):
     """Invalid parameters are refused with PSD_ERR_INVALID before any device
