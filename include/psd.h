@@ -170,6 +170,11 @@ enum {
  * psd_profile(h, 0) disables.                                              */
 psd_status psd_profile(psd_handle h, int enable);
 
+/* As psd_profile(h, 1), but brackets only the launches of the classes whose
+ * bit (1 << class) is set in mask (mask 0 disables).  Timing one class costs
+ * the others nothing.                                                       */
+psd_status psd_profile_classes(psd_handle h, unsigned mask);
+
 /* Accumulated device milliseconds and launch counts per kernel class since
  * the last psd_profile(h, 1) (synchronises the stream).  Kernels launched
  * after the stop flag is set return at once; the "effective" figures count

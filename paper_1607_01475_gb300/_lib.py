@@ -72,6 +72,7 @@ def load_library(build_if_missing=True):
     lib.psd_residual_f32.argtypes = [H, F, F, F]
     lib.psd_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
     lib.psd_profile.argtypes = [H, ctypes.c_int]
+    lib.psd_profile_classes.argtypes = [H, ctypes.c_uint]
     lib.psd_profile_read.argtypes = [H, P, P, P, P, ctypes.c_double, ctypes.c_int]
     lib.psd_profile_class_name.argtypes = [ctypes.c_int]
     lib.psd_profile_class_name.restype = ctypes.c_char_p
@@ -91,7 +92,8 @@ def load_library(build_if_missing=True):
     lib.psd_status_string.restype = ctypes.c_char_p
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
                  "psd_set_history", "psd_residual_f32", "psd_last_error", "psd_profile",
-                 "psd_profile_read", "psd_residual_noalloc", "psd_noalloc_last_error", "psd_hvp",
+                 "psd_profile_read", "psd_profile_classes", "psd_residual_noalloc", "psd_noalloc_last_error",
+                 "psd_hvp",
                  "psd_adjoint", "psd_batch_create", "psd_batch_solve", "psd_batch_destroy",
                  "psd_batch_last_error"):
         getattr(lib, name).restype = ctypes.c_int
@@ -316,8 +318,18 @@ class Solver:
     def adjoint(self, u, grad_u, grad_f, tol_rel=1e-12, max_iter=1000):
         return psd_adjoint(self.handle, u, grad_u, grad_f, tol_rel, max_iter)
 
-    def profile(self, enable=True):
-        _check(load_library().psd_profile(self.handle, 1 if enable else 0), self.handle)
+    def profile(self, enable=True, classes=None):
+        """Bracket kernel launches with events: all classes, or only the
+        class names in ``classes``."""
+        lib = load_library()
+        if classes is None or not enable:
+            _check(lib.psd_profile(self.handle, 1 if enable else 0), self.handle)
+            return
+        names = [lib.psd_profile_class_name(k).decode() for k in range(PSD_PROF_CLASSES)]
+        mask = 0
+        for c in classes:
+            mask |= 1 << names.index(c)
+        _check(lib.psd_profile_classes(self.handle, mask), self.handle)
 
     def profile_read(self, eff_us=8.0):
         """{class name: (ms, launches, effective ms, effective launches)}."""

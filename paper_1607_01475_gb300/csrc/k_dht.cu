@@ -20,6 +20,23 @@ template <>
 struct Vec2<double> {
   using type = double2;
 };
+struct __align__(16) ff2 {
+  ff x, y;
+};
+template <>
+struct Vec2<ff> {
+  using type = ff2;
+};
+
+// x * scale, skipping the (double-word) product when scale is 1
+template <typename T>
+__device__ __forceinline__ T scaled(T x, T scale) {
+  return x * scale;
+}
+template <>
+__device__ __forceinline__ ff scaled<ff>(ff x, ff scale) {
+  return (scale.hi == 1.0f && scale.lo == 0.0f) ? x : x * scale;
+}
 
 // Storage <-> compute element conversions (FP32, FP64, or float-float on
 // FP64 storage).
@@ -110,8 +127,8 @@ __global__ void __launch_bounds__(kThreads)
       const int k = j + q * F::TS;
       T h1, h2;
       dht_split(sr, si, k, N, h1, h2);
-      d0[k] = to_storage<S>(h1 * scale);
-      d0[N + k] = to_storage<S>(h2 * scale);
+      d0[k] = to_storage<S>(scaled(h1, scale));
+      d0[N + k] = to_storage<S>(scaled(h2, scale));
     }
   }
 }
@@ -150,8 +167,8 @@ __global__ void __launch_bounds__(kThreads)
     T h1, h2;
     dht_split(sr, si, k, N, h1, h2);
     V o;
-    o.x = to_storage<S>(h1 * scale);
-    o.y = to_storage<S>(h2 * scale);
+    o.x = to_storage<S>(scaled(h1, scale));
+    o.y = to_storage<S>(scaled(h2, scale));
     *reinterpret_cast<V*>(data + base + (size_t)k * line_stride) = o;
   }
 }
@@ -167,7 +184,7 @@ __global__ void __launch_bounds__(kThreads)
 enum { EPI_THETA = 0, EPI_RESID = 1 };
 template <int N, int RM, int EPI>
 __global__ void __launch_bounds__(kThreads)
-    k_dht_last_ff(const double* data, double* theta, float* out32, size_t line_stride, size_t outer_stride,
+    k_dht_last_ff(const ff* data, double* theta, float* out32, size_t line_stride, size_t outer_stride,
                   KParams kp, Ctrl* ctrl, double* partials, const ff* __restrict__ twc,
                   const ff* __restrict__ tws, const ff* __restrict__ symx, const ff* __restrict__ symo,
                   const ff* __restrict__ syml) {
@@ -192,10 +209,10 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
   for (int q = 0; q < F::R; ++q) {
     const size_t idx = base + (size_t)(j + q * F::TS) * line_stride;
-    const double2 v = *reinterpret_cast<const double2*>(data + idx);
+    const ff2 v = *reinterpret_cast<const ff2*>(data + idx);
     cp_async_16(pre + ((size_t)(q * F::TS + j) * pairs + p), theta + idx);
-    vr[q] = to_compute<T>(v.x);
-    vi[q] = to_compute<T>(v.y);
+    vr[q] = v.x;
+    vi[q] = v.y;
   }
   F::run(vr, vi, j, sr, si, twc, tws);
   cp_async_wait_all();
@@ -571,10 +588,9 @@ void set_attrs() {
   cudaFuncSetAttribute(k_mid<T, N, 4, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   cudaFuncSetAttribute(k_mid<T, N, 6, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPre);
   constexpr int RF = radix_pass<ff>();
-  cudaFuncSetAttribute(k_dht_rows<double, ff, N, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_dht_rows<double, ff, N, RF, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)kMaxSmem);
-  cudaFuncSetAttribute(k_dht_cols<double, ff, N, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_rows<ff, ff, N, RF, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_rows<ff, ff, N, RF, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  cudaFuncSetAttribute(k_dht_cols<ff, ff, N, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   cudaFuncSetAttribute(k_dht_last_ff<N, RF, EPI_THETA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kMaxSmemPre);
   cudaFuncSetAttribute(k_dht_last_ff<N, RF, EPI_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -602,29 +618,30 @@ cudaError_t launch_dht_rows(const T* src, T* dst, int nx, int nrows, T scale, co
   PSD_DISPATCH_N(nx, (rows_impl<T, T, NN>(src, dst, nrows, scale, done, tb.twc[0], tb.tws[0], st)));
 }
 
-cudaError_t launch_dht_rows_ff(const double* src, double* dst, int nx, int nrows, double scale,
-                               const AxisTables<ff>& tb, cudaStream_t st) {
-  PSD_DISPATCH_N(nx, (rows_impl<double, ff, NN>(src, dst, nrows, ff(scale), nullptr, tb.twc[0], tb.tws[0], st)));
+cudaError_t launch_dht_rows_ff(const double* src, ff* dst, int nx, int nrows, const AxisTables<ff>& tb,
+                               cudaStream_t st) {
+  PSD_DISPATCH_N(nx, (rows_impl<ff, ff, NN, double>(src, dst, nrows, ff(1.0f, 0.0f), nullptr, tb.twc[0], tb.tws[0],
+                                                     st)));
 }
 
-cudaError_t launch_dht_cols_ff(double* data, const KParams& kp, int ax, double scale, const AxisTables<ff>& tb,
-                               cudaStream_t st) {
+cudaError_t launch_dht_cols_ff(ff* data, const KParams& kp, int ax, const AxisTables<ff>& tb, cudaStream_t st) {
+  const ff scale(1.0f, 0.0f);
   const int n = ax == 1 ? kp.ny : kp.nz;
   const size_t line_stride = ax == 1 ? (size_t)kp.nx : (size_t)kp.nx * kp.ny;
   const size_t outer_stride = ax == 1 ? (size_t)kp.nx * kp.ny : (size_t)kp.nx;
   const int nouter = ax == 1 ? kp.nz : kp.ny;
-  PSD_DISPATCH_N(n, (cols_impl<double, ff, NN>(data, kp.nx, nouter, line_stride, outer_stride, ff(scale), nullptr,
-                                               tb.twc[ax], tb.tws[ax], st)));
+  PSD_DISPATCH_N(n, (cols_impl<ff, ff, NN>(data, kp.nx, nouter, line_stride, outer_stride, scale, nullptr,
+                                           tb.twc[ax], tb.tws[ax], st)));
 }
 
-cudaError_t launch_dht_rows_ff_from_f32(const float* src, double* dst, int nx, int nrows, const AxisTables<ff>& tb,
+cudaError_t launch_dht_rows_ff_from_f32(const float* src, ff* dst, int nx, int nrows, const AxisTables<ff>& tb,
                                         cudaStream_t st) {
-  PSD_DISPATCH_N(nx, (rows_impl<double, ff, NN, float>(src, dst, nrows, ff(1.0f, 0.0f), nullptr, tb.twc[0], tb.tws[0],
-                                                        st)));
+  PSD_DISPATCH_N(nx, (rows_impl<ff, ff, NN, float>(src, dst, nrows, ff(1.0f, 0.0f), nullptr, tb.twc[0], tb.tws[0],
+                                                    st)));
 }
 
 template <int N>
-cudaError_t last_ff_impl(const double* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
+cudaError_t last_ff_impl(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
                          double* partials, const AxisTables<ff>& tb, cudaStream_t st) {
   constexpr int RM = radix_pass<ff>();
   using F = LineFFT<ff, N, RM>;
@@ -650,7 +667,7 @@ cudaError_t last_ff_impl(const double* data, double* theta, float* out32, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_dht_last_ff(const double* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
+cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
                                double* partials, const AxisTables<ff>& tb, cudaStream_t st) {
   const int n = kp.dim == 3 ? kp.nz : kp.ny;
   PSD_DISPATCH_N(n, (last_ff_impl<NN>(data, theta, out32, kp, ctrl, partials, tb, st)));

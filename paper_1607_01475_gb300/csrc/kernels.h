@@ -28,19 +28,19 @@ template <typename T>
 cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const int* done,
                             const AxisTables<T>& tb, cudaStream_t st);
 
-// The same passes on FP64 data computed in float-float arithmetic (about 48
-// significant bits; tables of double-word twiddles).
-cudaError_t launch_dht_rows_ff(const double* src, double* dst, int nx, int nrows, double scale,
-                               const AxisTables<ff>& tb, cudaStream_t st);
-cudaError_t launch_dht_cols_ff(double* data, const KParams& kp, int ax, double scale, const AxisTables<ff>& tb,
+// Passes in float-float arithmetic (about 48 significant bits; tables of
+// double-word twiddles).  Between passes the data stays in float-float form
+// (hi, lo pairs in the 8 bytes of an FP64 element): the x pass reads FP64
+// (or FP32) and writes pairs; the strided pass transforms pairs in place.
+cudaError_t launch_dht_rows_ff(const double* src, ff* dst, int nx, int nrows, const AxisTables<ff>& tb,
                                cudaStream_t st);
-// The x pass reading FP32 lines (writes FP64).
-cudaError_t launch_dht_rows_ff_from_f32(const float* src, double* dst, int nx, int nrows, const AxisTables<ff>& tb,
+cudaError_t launch_dht_rows_ff_from_f32(const float* src, ff* dst, int nx, int nrows, const AxisTables<ff>& tb,
                                         cudaStream_t st);
+cudaError_t launch_dht_cols_ff(ff* data, const KParams& kp, int ax, const AxisTables<ff>& tb, cudaStream_t st);
 // The last pass (z in 3D, y in 2D) with a fused epilogue: out32 == nullptr:
 // theta += DHT(data) / mu; else out32 = (float)(DHT(data) - theta) and
 // ctrl->res_l2 = its Parseval norm (h^d / N sum)^{1/2}.  mu = 0 gives 0.
-cudaError_t launch_dht_last_ff(const double* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
+cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
                                double* partials, const AxisTables<ff>& tb, cudaStream_t st);
 
 // The middle pass along the slowest axis (y in 2D, z in 3D) of the

@@ -83,6 +83,7 @@ struct psd_context {
 
   // tracing: event pairs around every launch while enabled
   bool prof = false;
+  unsigned prof_mask = ~0u;  // classes bracketed while prof is on
   std::vector<cudaEvent_t> ev_pool;
   struct Rec {
     int cls;
@@ -241,7 +242,7 @@ struct ProfScope {
   int cls;
   int a = -1;
   ProfScope(psd_context* c_, int cls_) : c(c_), cls(cls_) {
-    if (!c->prof) return;
+    if (!c->prof || !((c->prof_mask >> cls_) & 1u)) return;
     const size_t need = 2 * (c->recs.size() + 1);
     if (need > c->ev_pool.size()) {
       if (c->ev_pool.size() >= 4096) {
@@ -308,32 +309,20 @@ psd_status full_dht(psd_context* c, T* x, T scale, const AxisTables<T>& tb) {
   return PSD_OK;
 }
 
-// Full separable DHT of FP64 data in float-float arithmetic (relative error
-// a few 2^-48 against ~2^-53 for FP64 arithmetic, at a fraction of the cost
-// on GB300, whose FP64 rate is 1/64 of its FP32 rate); scale a power of two.
-psd_status full_dht_ff(psd_context* c, double* x, double scale) {
-  const KParams& kp = c->kp;
-  const int nrows = kp.ny * kp.nz;
-  { ProfScope p_(c, PSD_PROF_DHT_ROWS_FF); CK(psd::launch_dht_rows_ff(x, x, kp.nx, nrows, 1.0, c->tbff, c->st)); }
-  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, kp.dim == 2 ? scale : 1.0, c->tbff, c->st)); }
-  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 2, scale, c->tbff, c->st)); }
-  return PSD_OK;
-}
-
 // theta += DHT(v) / mu (order 6, mixed): v is src64 (FP64, transformed in
 // place) or src32 (FP32, transformed into D); theta lives in Z.
-psd_status dht_theta_ff(psd_context* c, double* src64, const float* src32) {
+psd_status dht_theta_ff(psd_context* c, const double* src64, const float* src32) {
   const KParams& kp = c->kp;
   const int nrows = kp.ny * kp.nz;
-  double* x = src32 ? c->D : src64;
+  psd::ff* x = reinterpret_cast<psd::ff*>(c->D);  // float-float pairs between the passes
   if (src32) {
     ProfScope p_(c, PSD_PROF_DHT_ROWS_FF);
     CK(psd::launch_dht_rows_ff_from_f32(src32, x, kp.nx, nrows, c->tbff, c->st));
   } else {
     ProfScope p_(c, PSD_PROF_DHT_ROWS_FF);
-    CK(psd::launch_dht_rows_ff(x, x, kp.nx, nrows, 1.0, c->tbff, c->st));
+    CK(psd::launch_dht_rows_ff(src64, x, kp.nx, nrows, c->tbff, c->st));
   }
-  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, 1.0, c->tbff, c->st)); }
+  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, c->tbff, c->st)); }
   { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(x, c->Z, nullptr, kp, nullptr, c->partials, c->tbff, c->st)); }
   return PSD_OK;
 }
@@ -417,9 +406,10 @@ psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f
   ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
   const int nrows = kp.ny * kp.nz;
-  { ProfScope p_(c, PSD_PROF_DHT_ROWS_FF); CK(psd::launch_dht_rows_ff(c->W, c->W, kp.nx, nrows, 1.0, c->tbff, c->st)); }
-  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(c->W, kp, 1, 1.0, c->tbff, c->st)); }
-  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(c->W, c->Z, c->R32, kp, c->ctrl2, c->partials, c->tbff, c->st)); }
+  psd::ff* x = reinterpret_cast<psd::ff*>(c->W);  // transformed in place, float-float pairs after the x pass
+  { ProfScope p_(c, PSD_PROF_DHT_ROWS_FF); CK(psd::launch_dht_rows_ff(c->W, x, kp.nx, nrows, c->tbff, c->st)); }
+  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, c->tbff, c->st)); }
+  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(x, c->Z, c->R32, kp, c->ctrl2, c->partials, c->tbff, c->st)); }
   Ctrl h2;
   TRY(read_ctrl(c, c->ctrl2, h2));
   *res = h2.res_l2;
@@ -732,6 +722,14 @@ psd_status psd_profile(psd_handle c, int enable) {
     TRY(prof_flush(c));
   }
   c->prof = enable != 0;
+  c->prof_mask = ~0u;
+  return PSD_OK;
+}
+
+psd_status psd_profile_classes(psd_handle c, unsigned mask) {
+  if (!c) return PSD_ERR_INVALID;
+  TRY(psd_profile(c, mask != 0 ? 1 : 0));
+  c->prof_mask = mask;
   return PSD_OK;
 }
 
