@@ -13,6 +13,7 @@
 // (2 vertex planes) in shared memory.  Every vertex flux and every Laplacian
 // value is computed once per CTA.
 #include <cmath>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -623,6 +624,41 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+// max |G|^2 over the vertices of an FP32 field (one vertex per thread,
+// grid-stride over the vertex planes; G from the 8 surrounding cells).
+__global__ void __launch_bounds__(NT) k_gradmax(const float* __restrict__ u, KParams kp, Ctrl* ctrl,
+                                                double* partials) {
+  __shared__ float sred[32];
+  __shared__ int sflag;
+  const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+  const int lx = __ffs(nx) - 1, lxy = lx + __ffs(ny) - 1;  // sizes are powers of two
+  const size_t plane = (size_t)nx * ny, n = plane * nz;
+  float m = 0.0f;
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    const int x = (int)(i & (nx - 1)), y = (int)((i >> lx) & (ny - 1)), z = (int)(i >> lxy);
+    const int x1 = (x + 1) & (nx - 1), y1 = (y + 1) & (ny - 1), z1 = (z + 1) & (nz - 1);
+    const size_t r0 = (size_t)z * plane, r1 = (size_t)z1 * plane;
+    const float u000 = u[r0 + (size_t)y * nx + x], u001 = u[r0 + (size_t)y * nx + x1];
+    const float u010 = u[r0 + (size_t)y1 * nx + x], u011 = u[r0 + (size_t)y1 * nx + x1];
+    const float u100 = u[r1 + (size_t)y * nx + x], u101 = u[r1 + (size_t)y * nx + x1];
+    const float u110 = u[r1 + (size_t)y1 * nx + x], u111 = u[r1 + (size_t)y1 * nx + x1];
+    const float g0 = ((u001 - u000) + (u011 - u010)) + ((u101 - u100) + (u111 - u110));
+    const float g1 = ((u010 - u000) + (u011 - u001)) + ((u110 - u100) + (u111 - u101));
+    const float g2 = ((u100 - u000) + (u101 - u001)) + ((u110 - u010) + (u111 - u011));
+    m = fmaxf(m, g0 * g0 + g1 * g1 + g2 * g2);
+  }
+  float v[1] = {m};
+  block_reduce<float, 1, true>(v, sred);
+  if (publish_and_check_last<float>(v, 1, reinterpret_cast<float*>(partials), &ctrl->counter[CS_MID], &sflag)) {
+    float tt[1];
+    gather_partials<float, 1, true>(tt, reinterpret_cast<const float*>(partials), sred);
+    if (threadIdx.x == 0) {
+      ctrl->res_linf = (double)tt[0];
+      ctrl->counter[CS_MID] = 0;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ misc
 template <typename T>
 __global__ void k_axpby(T* y, const T* x, const T* z, double a, double b, double c, size_t n) {
@@ -741,6 +777,12 @@ cudaError_t res_impl(const ResArgs<T>& a, const KParams& kp, Ctrl* ctrl, double*
       if constexpr (sizeof(T) == 4) k_res3d_rb<T, PK, MODE, 4><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
       break;
     case RK_COL:
+      if constexpr (sizeof(T) == 8 && MODE == RM_PLAIN && PK == PK_4) {
+        if (a.fluxff) {
+          k_res3d_col<T, PK, MODE, true><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
+          break;
+        }
+      }
       k_res3d_col<T, PK, MODE><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
       break;
     case RK_SMALL3D:
@@ -813,6 +855,11 @@ cudaError_t launch_axpby(T* y, const T* x, const T* z, double a, double b, doubl
 cudaError_t launch_dot(const double* x, const double* y, const double* z, size_t n, Ctrl* c, double* partials,
                        cudaStream_t st) {
   k_dot<<<std::min(grid1d(n), 1024), NT, 0, st>>>(x, y, z, n, c, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_gradmax(const float* u, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st) {
+  const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
+  k_gradmax<<<std::min(grid1d(n), 1024), NT, 0, st>>>(u, kp, ctrl, partials);
   return cudaGetLastError();
 }
 cudaError_t launch_norms(const double* x, size_t n, double hd, Ctrl* c, double* partials, cudaStream_t st) {

@@ -82,6 +82,7 @@ struct ResArgs {
   T* r;            // residual (order 6: local part, without T_h)
   int norm;        // 1: reduce ||r|| into ctrl and decide convergence
   int update_iter; // 1: this call advances the iteration count
+  int fluxff;      // FP64 plain, p = 4, 3D: flux part in float-float (see k_res3d_col)
 };
 
 // r = f - N_h^{loc}[u_in + alpha d] (plain) or
@@ -97,6 +98,11 @@ cudaError_t launch_residual(const ResArgs<T>& a, int mode, int pk, const KParams
 template <typename T>
 cudaError_t launch_linesearch(const T* u, const T* ubase, const T* d, int pk, const KParams& kp,
                               Ctrl* ctrl, double* partials, cudaStream_t st);
+
+// max over vertices of |G|^2, G the unscaled vertex gradient sums of the
+// FP32 field u (g = q G), into ctrl->res_linf (an estimate for choosing the
+// float-float flux of the FP64 residual).  3D grids with nx >= 32, ny >= 8.
+cudaError_t launch_gradmax(const float* u, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st);
 
 // Number of blocks launch_residual<T> uses for this problem size (one
 // partial sum record per block); fp32 = (T is float).

@@ -373,14 +373,38 @@ psd_status ensure_fp32(psd_context* c) {
   return PSD_OK;
 }
 
+// Whether the FP64 residual of the current iterate (its FP32 copy in u32)
+// may evaluate the flux part in float-float: p = 4, 3D column kernel, and
+// a worst-case error bound of that part,
+//   |Omega|^{1/2} * 24 * 2^-47 * s q^4 * (2 max|G|)^3
+// (24 flux values per cell in the divergence, 2^-47 the double-word
+// precision, a factor 2 of margin on the FP32 estimate of max|G|), below
+// tol / 20.
+psd_status use_fluxff(psd_context* c, bool* out) {
+  *out = false;
+  const KParams& kp = c->kp;
+  if (c->pk != psd::PK_4 || kp.dim != 3 || kp.nx < 32 || kp.ny < 8 || !(c->prm.tol > 0)) return PSD_OK;
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_gradmax(c->u32, kp, c->ctrl2, c->partials, c->st)); }
+  Ctrl h2;
+  TRY(read_ctrl(c, c->ctrl2, h2));
+  const double gmax = 2.0 * std::sqrt(std::max(h2.res_linf, 0.0));
+  const double bound = std::sqrt((double)c->N * kp.hd) * 24.0 * std::ldexp(1.0, -47) * kp.cdiv * gmax * gmax * gmax;
+  *out = std::isfinite(bound) && bound < 0.05 * c->prm.tol;
+  return PSD_OK;
+}
+
 // FP64 residual r = f - N_h[u] into r (order 6: P0[...] including T_h[u - g]),
 // norms into ctrl2 (res_l2, res_linf).  Uses W, Z as scratch (order 6).
-psd_status residual64(psd_context* c, const double* u, const double* f, const double* g, double* r) {
+psd_status residual64(psd_context* c, const double* u, const double* f, const double* g, double* r,
+                      bool fluxff = false) {
   const KParams& kp = c->kp;
   Ctrl h;
   init_ctrl(h, -1.0, 1 << 30);
   TRY(upload_ctrl(c, c->ctrl2, h));
-  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, r, kp.order == 4 ? 1 : 0, 0};
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, r, kp.order == 4 ? 1 : 0, 0, fluxff ? 1 : 0};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
   if (kp.order == 6) {
     // r <- P0[r_loc - T_h[u - g]] through the spectrum
@@ -398,12 +422,12 @@ psd_status residual64(psd_context* c, const double* u, const double* f, const do
 // R32 <- (float) DHT(P0[f - N_h^{loc}[u]] - T_h[u - g]) = DHT(r_loc) - theta
 // with theta = DHT(T_h[u - g]) in Z (the subtraction, the rounding and the
 // Parseval norm fused into the last transform pass); ||R||_2 into *res.
-psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f, double* res) {
+psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f, double* res, bool fluxff) {
   const KParams& kp = c->kp;
   Ctrl h;
   init_ctrl(h, -1.0, 1 << 30);
   TRY(upload_ctrl(c, c->ctrl2, h));
-  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0};
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0, fluxff ? 1 : 0};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
   const int nrows = kp.ny * kp.nz;
   psd::ff* x = reinterpret_cast<psd::ff*>(c->W);  // transformed in place, float-float pairs after the x pass
@@ -517,13 +541,15 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
         { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
       }
     }
+    bool fluxff = false;
+    TRY(use_fluxff(c, &fluxff));
     if (six) {
       // the outer residual stays in the transform domain; the inner solve adds
       // it to its own transformed residual in the middle pass
-      TRY(outer_residual6_spec(c, u, f, &res));
+      TRY(outer_residual6_spec(c, u, f, &res, fluxff));
       resinf = -1.0;
     } else {
-      TRY(residual64(c, u, f, g, c->W));
+      TRY(residual64(c, u, f, g, c->W, fluxff));
       Ctrl h2;
       TRY(read_ctrl(c, c->ctrl2, h2));
       res = h2.res_l2;

@@ -34,9 +34,17 @@
 namespace psd {
 namespace {
 
-template <typename T, int PK, int MODE>
+// FFX (FP64, plain mode, p = 4): the flux part -- |G|^2 G, its z-sums S and
+// the divergence -- is evaluated in float-float arithmetic from the FP64
+// vertex gradients, halving the FP64 operations per cell; the gradients,
+// both Laplacian passes and the residual stay FP64.  The caller selects it
+// only when the worst-case float-float error of that part is far below the
+// solve tolerance (it scales with s q^4 max|G|^3).
+template <typename T, int PK, int MODE, bool FFX = false>
 __global__ void __launch_bounds__(256, 2)
     k_res3d_col(ResArgs<T> a, KParams kp, Ctrl* ctrl, double* partials, int zc) {
+  static_assert(!FFX || (sizeof(T) == 8 && MODE == RM_PLAIN && PK == PK_4), "FFX: FP64 plain p = 4 only");
+  using FT = typename std::conditional<FFX, ff, T>::type;  // arithmetic type of the flux part
   if (ctrl->done) return;
   constexpr int TX = 32, TY = 8;
   constexpr int UX = TX + 4, UY = TY + 4, UN = UX * UY;  // U tile, halo 2
@@ -189,12 +197,18 @@ __global__ void __launch_bounds__(256, 2)
     return own;
   };
   // Phi at vertex (vy, vx) of the current vertex plane (from sP/sM)
-  auto vphi = [&](int vy, int vx, T (&F)[3]) {
+  auto vphi = [&](int vy, int vx, FT (&F)[3]) {
     T G[3];
     G[0] = (sP[vy][vx + 1] - sP[vy][vx]) + (sP[vy + 1][vx + 1] - sP[vy + 1][vx]);
     G[1] = (sP[vy + 1][vx] - sP[vy][vx]) + (sP[vy + 1][vx + 1] - sP[vy][vx + 1]);
     G[2] = (sM[vy][vx] + sM[vy][vx + 1]) + (sM[vy + 1][vx] + sM[vy + 1][vx + 1]);
-    if (BASE) {
+    if constexpr (FFX) {
+      const ff g0 = ff_from_double_bits(G[0]), g1 = ff_from_double_bits(G[1]), g2 = ff_from_double_bits(G[2]);
+      const ff q2 = ff_add_fast(ff_add_fast(g0 * g0, g1 * g1), g2 * g2);
+      F[0] = q2 * g0;
+      F[1] = q2 * g1;
+      F[2] = q2 * g2;
+    } else if (BASE) {
       T A[3];
       A[0] = (sPb[vy][vx + 1] - sPb[vy][vx]) + (sPb[vy + 1][vx + 1] - sPb[vy + 1][vx]);
       A[1] = (sPb[vy + 1][vx] - sPb[vy][vx]) + (sPb[vy + 1][vx + 1] - sPb[vy][vx + 1]);
@@ -207,18 +221,21 @@ __global__ void __launch_bounds__(256, 2)
       flux<PK>(G, beta, F);
     }
   };
+  // the S sums in the arithmetic type of the flux (float-float pairs occupy
+  // the 8 bytes of an FP64 slot)
+  FT(*SS)[VY][VX] = reinterpret_cast<FT(*)[VY][VX]>(&sS[0][0][0]);
   // own vertex (ty+1, tx+1) and, for tid < NVH, one halo vertex
   const bool hv = tid < NVH;
   const int hvy = tid < VY ? tid : 0;
   const int hvx = tid < VY ? 0 : tid - VY + 1;
-  T Fo[3] = {T(0), T(0), T(0)}, Fh[3] = {T(0), T(0), T(0)};  // Phi of the previous vertex plane
+  FT Fo[3] = {FT(0), FT(0), FT(0)}, Fh[3] = {FT(0), FT(0), FT(0)};  // Phi of the previous vertex plane
   auto phi_plane = [&](bool first) {
-    T F[3];
+    FT F[3];
     vphi(ty + 1, tx + 1, F);
     if (!first) {
-      sS[0][ty + 1][tx + 1] = Fo[0] + F[0];
-      sS[1][ty + 1][tx + 1] = Fo[1] + F[1];
-      sS[2][ty + 1][tx + 1] = F[2] - Fo[2];
+      SS[0][ty + 1][tx + 1] = Fo[0] + F[0];
+      SS[1][ty + 1][tx + 1] = Fo[1] + F[1];
+      SS[2][ty + 1][tx + 1] = F[2] - Fo[2];
     }
     Fo[0] = F[0];
     Fo[1] = F[1];
@@ -226,9 +243,9 @@ __global__ void __launch_bounds__(256, 2)
     if (hv) {
       vphi(hvy, hvx, F);
       if (!first) {
-        sS[0][hvy][hvx] = Fh[0] + F[0];
-        sS[1][hvy][hvx] = Fh[1] + F[1];
-        sS[2][hvy][hvx] = F[2] - Fh[2];
+        SS[0][hvy][hvx] = Fh[0] + F[0];
+        SS[1][hvy][hvx] = Fh[1] + F[1];
+        SS[2][hvy][hvx] = F[2] - Fh[2];
       }
       Fh[0] = F[0];
       Fh[1] = F[1];
@@ -283,10 +300,14 @@ __global__ void __launch_bounds__(256, 2)
     const T bih = (((sL[lz][ty + 1][tx] + sL[lz][ty + 1][tx + 2]) + (sL[lz][ty][tx + 1] + sL[lz][ty + 2][tx + 1])) +
                    (Lm + Lp)) -
                   T(6) * L0;
-    const T dx = (sS[0][ty][tx + 1] - sS[0][ty][tx]) + (sS[0][ty + 1][tx + 1] - sS[0][ty + 1][tx]);
-    const T dy = (sS[1][ty + 1][tx] - sS[1][ty][tx]) + (sS[1][ty + 1][tx + 1] - sS[1][ty][tx + 1]);
-    const T dz = (sS[2][ty][tx] + sS[2][ty][tx + 1]) + (sS[2][ty + 1][tx] + sS[2][ty + 1][tx + 1]);
-    const T div = (dx + dy) + dz;
+    const FT dx = (SS[0][ty][tx + 1] - SS[0][ty][tx]) + (SS[0][ty + 1][tx + 1] - SS[0][ty + 1][tx]);
+    const FT dy = (SS[1][ty + 1][tx] - SS[1][ty][tx]) + (SS[1][ty + 1][tx + 1] - SS[1][ty][tx + 1]);
+    const FT dz = (SS[2][ty][tx] + SS[2][ty][tx + 1]) + (SS[2][ty + 1][tx] + SS[2][ty + 1][tx + 1]);
+    T div;
+    if constexpr (FFX)
+      div = ff_to_double_bits((dx + dy) + dz);
+    else
+      div = (dx + dy) + dz;
     T r;
     if (INNER)
       r = fcur - ((cu * uc + cbih * bih) - cdiv * div);
