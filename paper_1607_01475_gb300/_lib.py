@@ -13,7 +13,7 @@ _LIB_NAME = "libpsd.so"
 
 PSD_FP64 = 0
 PSD_MIXED = 1
-PSD_PROF_CLASSES = 13  # kernel classes of psd_profile_read
+PSD_PROF_CLASSES = 14  # kernel classes of psd_profile_read
 
 _STATUS = {0: "PSD_OK", 1: "PSD_ERR_INVALID", 2: "PSD_ERR_NOMEM", 3: "PSD_ERR_CUDA",
            4: "PSD_ERR_NOCONV", 5: "PSD_ERR_TIMEOUT", 6: "PSD_ERR_UNSUPPORTED",
@@ -70,6 +70,7 @@ def load_library(build_if_missing=True):
     lib.psd_solve.argtypes = [H, D, D, D, D, ctypes.POINTER(PSDInfo)]
     lib.psd_set_history.argtypes = [H, P, P, ctypes.c_int]
     lib.psd_residual_f32.argtypes = [H, F, F, F]
+    lib.psd_precond_solve_f32.argtypes = [H, F, F]
     lib.psd_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
     lib.psd_profile.argtypes = [H, ctypes.c_int]
     lib.psd_profile_classes.argtypes = [H, ctypes.c_uint]
@@ -93,6 +94,7 @@ def load_library(build_if_missing=True):
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
                  "psd_set_history", "psd_residual_f32", "psd_last_error", "psd_profile",
                  "psd_profile_read", "psd_profile_classes", "psd_residual_noalloc", "psd_noalloc_last_error",
+                 "psd_precond_solve_f32",
                  "psd_hvp",
                  "psd_adjoint", "psd_batch_create", "psd_batch_solve", "psd_batch_destroy",
                  "psd_batch_last_error"):
@@ -185,6 +187,10 @@ def psd_adjoint(handle, u, grad_u, grad_f, tol_rel=1e-12, max_iter=1000):
     _check(load_library().psd_adjoint(handle, _ptr(u), _ptr(grad_u), _ptr(grad_f), ctypes.byref(gs),
                                       tol_rel, max_iter, ctypes.byref(info)), handle)
     return gs.value, info.as_dict()
+
+
+def psd_precond_solve_f32(handle, r, d):
+    _check(load_library().psd_precond_solve_f32(handle, _ptr(r, "float32"), _ptr(d, "float32")), handle)
 
 
 def psd_residual_f32(handle, u, f, r):
@@ -293,6 +299,9 @@ class Solver:
 
     def residual_f32(self, u, f, r):
         psd_residual_f32(self.handle, u, f, r)
+
+    def precond_solve_f32(self, r, d):
+        psd_precond_solve_f32(self.handle, r, d)
 
     def set_history(self, cap):
         import numpy as np

@@ -333,6 +333,15 @@ psd_status precond_passes(psd_context* c, T* W, T* D, Ctrl* ctrl, T* xi, T* dspe
   const KParams& kp = c->kp;
   const int* done = &ctrl->done;
   const int nrows = kp.ny * kp.nz;
+  if constexpr (sizeof(T) == 4) {
+    if (psd::dht_xy_supported(kp)) {
+      // forward x, y in one cluster kernel; z, symbol and inverse z; inverse x, y
+      { ProfScope p_(c, PSD_PROF_DHT_XY_FP32); CK(psd::launch_dht_xy(W, W, kp, done, tb, c->st)); }
+      { ProfScope p_(c, PSD_PROF_MID_FP32); CK(psd::launch_mid<T>(W, kp, ctrl, c->partials, xi, dspec, tb, c->st)); }
+      { ProfScope p_(c, PSD_PROF_DHT_XY_FP32); CK(psd::launch_dht_xy(W, D, kp, done, tb, c->st)); }
+      return PSD_OK;
+    }
+  }
   { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_ROWS_FP64)); CK(psd::launch_dht_rows<T>(W, W, kp.nx, nrows, T(1), done, tb, c->st)); }
   if (kp.dim == 3) { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_COLS_FP64)); CK(psd::launch_dht_cols<T>(W, kp, 1, T(1), done, tb, c->st)); }
   { ProfScope p_(c, cls_of<T>(PSD_PROF_MID_FP64)); CK(psd::launch_mid<T>(W, kp, ctrl, c->partials, xi, dspec, tb, c->st)); }
@@ -783,7 +792,7 @@ const char* psd_profile_class_name(int k) {
   static const char* names[PSD_PROF_CLASSES] = {
       "residual_fp64", "residual_fp32", "dht_rows_fp64", "dht_rows_fp32", "dht_cols_fp64", "dht_cols_fp32",
       "mid_fp64",      "mid_fp32",      "linesearch_fp64", "linesearch_fp32", "other",
-      "dht_rows_ff",   "dht_cols_ff"};
+      "dht_rows_ff",   "dht_cols_ff",   "dht_xy_fp32"};
   return (k >= 0 && k < PSD_PROF_CLASSES) ? names[k] : nullptr;
 }
 
@@ -851,6 +860,22 @@ psd_status psd_precond_solve(psd_handle c, const double* r, double* d) {
     CK(cudaMemsetAsync(c->Dsp, 0, c->N * sizeof(double), c->st));
   }
   TRY(precond_passes<double>(c, d, d, c->ctrl2, c->Z, c->Dsp, c->tb64));
+  return PSD_OK;
+}
+
+psd_status psd_precond_solve_f32(psd_handle c, const float* r, float* d) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!r || !d) return fail(c, PSD_ERR_INVALID, "r and d are required");
+  TRY(ensure_fp32(c));
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  if (d != r) CK(cudaMemcpyAsync(d, r, c->N * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+  if (c->prm.order == 6) {
+    CK(cudaMemsetAsync(c->R32, 0, c->N * sizeof(float), c->st));
+    CK(cudaMemsetAsync(c->Dsp32, 0, c->N * sizeof(float), c->st));
+  }
+  TRY(precond_passes<float>(c, d, d, c->ctrl2, c->prm.order == 6 ? c->R32 : nullptr, c->Dsp32, c->tb32));
   return PSD_OK;
 }
 

@@ -130,6 +130,28 @@ def test_mixed_solve_register_blocked(p):
 
 # ---------------------------------------------------------- preconditioner
 
+@pytest.mark.parametrize("shape", [(32, 64, 64), (16, 128, 128), (8, 256, 256), (16, 32, 64), (64, 64)])
+@pytest.mark.parametrize("order", [4, 6])
+def test_precond_f32_parity(oracle, shape, order):
+    """The FP32 preconditioner of the inner solve (the fused x/y cluster
+    pass for nx = ny in {64, 128, 256}, separate passes otherwise) against
+    the FP64 oracle.  FP32 transform rounding is ~log2(N) eps32 of the
+    input's norm; a smooth input keeps d = L_h^{-1} r of the same size as r
+    (for white noise d is ~1e-2 of r and the bound would be ~1e-4)."""
+    P, h = _problem(oracle, order, shape, 4.0)
+    r = smooth_random(shape, K=6, seed=7)
+    S = Solver(order, shape, h, 4.0, P.s, P.eps, P.lam, precision=PSD_MIXED)
+    r32 = torch.from_numpy(r.astype(np.float32)).cuda()
+    d = torch.empty_like(r32)
+    S.precond_solve_f32(r32, d)
+    ref = oracle.precond4(r.astype(np.float32).astype(np.float64), P) if order == 4 else \
+        oracle.precond6(r.astype(np.float32).astype(np.float64), P)
+    assert rel(host(d).astype(np.float64), ref) <= 2e-5
+    rd = r32.clone()
+    S.precond_solve_f32(rd, rd)  # in place
+    assert torch.equal(rd, d)
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("order", [4, 6])
 def test_precond_parity(oracle, shape, order):
