@@ -74,6 +74,16 @@ typedef struct psd_params {
                        this factor; 0 = default (1e-4); in [0, 1)               */
   int inner_stall;  /* ... or when that norm has not halved in this many
                        iterations (its FP32 floor); 0 = default (5)            */
+  /* Optional device allocator for the handle's workspace (both NULL:
+   * cudaMalloc / cudaFree).  alloc(bytes, alloc_ctx) returns device memory
+   * aligned to 256 bytes or NULL; free_fn(ptr, alloc_ctx) releases it.  Every
+   * workspace allocation of the handle goes through them, in psd_create or
+   * on first use of a precision, and psd_destroy returns all of it.        */
+  void* (*alloc)(size_t bytes, void* alloc_ctx);
+  void (*free_fn)(void* ptr, void* alloc_ctx);
+  void* alloc_ctx;
+  int report_energy; /* 1: psd_solve also evaluates E_h of the result into
+                        psd_info.energy (one extra FP64 pass)               */
 } psd_params;
 
 typedef struct psd_info {
@@ -81,6 +91,8 @@ typedef struct psd_info {
   int outer_iters;    /* mixed: FP64 outer residual evaluations               */
   double res_l2;      /* final ||f - N_h[u]||_2 (order 6: mean-projected)     */
   double res_linf;    /* final max |r| (order 4 FP64; -1 when not formed)     */
+  double energy;      /* E_h of the result when report_energy was set (Sec.
+                         5.3 / 5.4 discrete energies), else NaN              */
   double last_alpha;  /* last step size                                       */
   double wall_ms;     /* device time of the solve (CUDA events)               */
   int status;         /* psd_status of the solve                              */
@@ -103,6 +115,12 @@ psd_status psd_destroy(psd_handle h);
 psd_status psd_residual(psd_handle h, const double* u, const double* f,
                         const double* g, double* r, double* res_l2,
                         double* res_linf);
+
+/* Discrete energy E_h[u] (Sec. 5.3, Eq. "diseng4"; order 6: Sec. 5.4 in the
+ * u = nu + mean(g) variables) into *energy (host).  FP64; synchronises the
+ * handle's stream.  g is required for order 6.                             */
+psd_status psd_energy(psd_handle h, const double* u, const double* f,
+                      const double* g, double* energy);
 
 /* Search direction: solve L_h d = r by the FFT (Sec. 6; symbol of L_h from
  * Sec. 5.3 / 5.4).  Order 6 returns the mean-zero solution for P0 r.

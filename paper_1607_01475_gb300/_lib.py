@@ -20,18 +20,36 @@ _STATUS = {0: "PSD_OK", 1: "PSD_ERR_INVALID", 2: "PSD_ERR_NOMEM", 3: "PSD_ERR_CU
            7: "PSD_ERR_NONFINITE"}
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class PSDParams(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
                 ("h", ctypes.c_double), ("p", ctypes.c_double), ("s", ctypes.c_double),
                 ("eps", ctypes.c_double), ("lam", ctypes.c_double), ("precision", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_outer", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("inner_eta", ctypes.c_double), ("inner_stall", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("inner_eta", ctypes.c_double), ("inner_stall", ctypes.c_int),
+                ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("report_energy", ctypes.c_int)]
 
 
 class PSDInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("res_l2", ctypes.c_double),
-                ("res_linf", ctypes.c_double), ("last_alpha", ctypes.c_double),
+                ("res_linf", ctypes.c_double), ("energy", ctypes.c_double), ("last_alpha", ctypes.c_double),
                 ("wall_ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+# ctypes callback objects must outlive the handle that calls them
+_callbacks = {}
+
+
+def _allocator_callbacks(allocator):
+    """(alloc(nbytes) -> int device pointer, free(int pointer)) -> ctypes pair."""
+    if allocator is None:
+        return ALLOC_FN(), FREE_FN()
+    a, f = allocator
+    return ALLOC_FN(lambda n, ctx: a(n)), FREE_FN(lambda ptr, ctx: f(ptr))
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,6 +89,7 @@ def load_library(build_if_missing=True):
     lib.psd_set_history.argtypes = [H, P, P, ctypes.c_int]
     lib.psd_residual_f32.argtypes = [H, F, F, F]
     lib.psd_precond_solve_f32.argtypes = [H, F, F]
+    lib.psd_energy.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.psd_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
     lib.psd_profile.argtypes = [H, ctypes.c_int]
     lib.psd_profile_classes.argtypes = [H, ctypes.c_uint]
@@ -94,7 +113,7 @@ def load_library(build_if_missing=True):
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
                  "psd_set_history", "psd_residual_f32", "psd_last_error", "psd_profile",
                  "psd_profile_read", "psd_profile_classes", "psd_residual_noalloc", "psd_noalloc_last_error",
-                 "psd_precond_solve_f32",
+                 "psd_precond_solve_f32", "psd_energy",
                  "psd_hvp",
                  "psd_adjoint", "psd_batch_create", "psd_batch_solve", "psd_batch_destroy",
                  "psd_batch_last_error"):
@@ -136,22 +155,30 @@ def _stream_handle(stream):
 # ------------------------------------------------------------ C-named calls
 
 def psd_create(order, shape, h, p, s, eps, lam=0.0, precision=PSD_FP64, tol=1e-10,
-               max_iter=10000, max_outer=20, stream=None, inner_eta=0.0, inner_stall=0):
-    """Create a solver handle for a grid of ``shape`` ((ny, nx) or (nz, ny, nx))."""
+               max_iter=10000, max_outer=20, stream=None, inner_eta=0.0, inner_stall=0, allocator=None,
+               report_energy=False):
+    """Create a solver handle for a grid of ``shape`` ((ny, nx) or (nz, ny, nx)).
+    ``allocator``: optional (alloc(nbytes) -> device pointer, free(pointer))."""
     lib = load_library()
     dim = len(shape)
     n = (shape[-1], shape[-2], shape[0] if dim == 3 else 1)
+    cb_alloc, cb_free = _allocator_callbacks(allocator)
     prm = PSDParams(order=order, dim=dim, n=(ctypes.c_int * 3)(*n), h=h, p=p, s=s, eps=eps, lam=lam,
                     precision=precision, tol=tol, max_iter=max_iter, max_outer=max_outer,
                     stream=_stream_handle(stream) if stream is not False else None,
-                    inner_eta=inner_eta, inner_stall=inner_stall)
+                    inner_eta=inner_eta, inner_stall=inner_stall, alloc=cb_alloc, free_fn=cb_free,
+                    report_energy=1 if report_energy else 0)
     out = ctypes.c_void_p()
     _check(lib.psd_create(ctypes.byref(prm), ctypes.byref(out)), None)
+    if allocator is not None:
+        _callbacks[out.value] = (cb_alloc, cb_free)
     return out
 
 
 def psd_destroy(handle):
-    return load_library().psd_destroy(handle)
+    st = load_library().psd_destroy(handle)
+    _callbacks.pop(getattr(handle, "value", handle), None)
+    return st
 
 
 def psd_residual(handle, u, f, g=None, r=None):
@@ -187,6 +214,12 @@ def psd_adjoint(handle, u, grad_u, grad_f, tol_rel=1e-12, max_iter=1000):
     _check(load_library().psd_adjoint(handle, _ptr(u), _ptr(grad_u), _ptr(grad_f), ctypes.byref(gs),
                                       tol_rel, max_iter, ctypes.byref(info)), handle)
     return gs.value, info.as_dict()
+
+
+def psd_energy(handle, u, f, g=None):
+    e = ctypes.c_double()
+    _check(load_library().psd_energy(handle, _ptr(u), _ptr(f), _ptr(g), ctypes.byref(e)), handle)
+    return e.value
 
 
 def psd_precond_solve_f32(handle, r, d):
@@ -274,10 +307,11 @@ class Solver:
     """Owns one handle.  ``shape`` is (ny, nx) or (nz, ny, nx)."""
 
     def __init__(self, order, shape, h, p, s, eps, lam=0.0, precision=PSD_FP64, tol=1e-10,
-                 max_iter=10000, max_outer=20, stream=None, inner_eta=0.0, inner_stall=0):
+                 max_iter=10000, max_outer=20, stream=None, inner_eta=0.0, inner_stall=0, allocator=None,
+                 report_energy=False):
         self.shape = tuple(shape)
         self.handle = psd_create(order, shape, h, p, s, eps, lam, precision, tol, max_iter,
-                                 max_outer, stream, inner_eta, inner_stall)
+                                 max_outer, stream, inner_eta, inner_stall, allocator, report_energy)
         self._hist = None
 
     def close(self):
@@ -302,6 +336,9 @@ class Solver:
 
     def precond_solve_f32(self, r, d):
         psd_precond_solve_f32(self.handle, r, d)
+
+    def energy(self, u, f, g=None):
+        return psd_energy(self.handle, u, f, g)
 
     def set_history(self, cap):
         import numpy as np

@@ -470,6 +470,28 @@ __global__ void k_spec6_combine(T* a, const T* b, KParams kp, const T* sx, const
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_spec_quad(const T* a, KParams kp, const T* sx, const T* sy, const T* sz,
+                                                   size_t n, Ctrl* ctrl, double* partials) {
+  __shared__ double sred[32];
+  __shared__ int sflag;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double mu = (double)mu_at(i, kp, sx, sy, sz);
+    if (mu > 0.0) acc += (double)a[i] * (double)a[i] / mu;
+  }
+  double v[1] = {acc};
+  block_reduce<double, 1, false>(v, sred);
+  if (publish_and_check_last<double>(v, 1, partials, &ctrl->counter[CS_MID], &sflag)) {
+    double tt[1];
+    gather_partials<double, 1, false>(tt, partials, sred);
+    if (threadIdx.x == 0) {
+      ctrl->rd = tt[0];
+      ctrl->counter[CS_MID] = 0;
+    }
+  }
+}
+
 __global__ void k_widen_f64(double* out, const float* in, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (double)in[i];
@@ -715,6 +737,17 @@ cudaError_t launch_spec_apply_T(T* a, T scale, const KParams& kp, const AxisTabl
   k_spec_apply_T<T><<<grid, 256, 0, st>>>(a, scale, kp, tb.sym[0], tb.sym[1], tb.sym[2], n);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_spec_quad(const T* a, const KParams& kp, Ctrl* ctrl, double* partials, const AxisTables<T>& tb,
+                             cudaStream_t st) {
+  const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 1024);
+  k_spec_quad<T><<<grid, 256, 0, st>>>(a, kp, tb.sym[0], tb.sym[1], tb.sym[2], n, ctrl, partials);
+  return cudaGetLastError();
+}
+template cudaError_t launch_spec_quad<double>(const double*, const KParams&, Ctrl*, double*, const AxisTables<double>&,
+                                              cudaStream_t);
 
 cudaError_t launch_widen_f64(double* out, const float* in, size_t n, cudaStream_t st) {
   const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);

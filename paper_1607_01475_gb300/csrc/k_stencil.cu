@@ -659,6 +659,70 @@ __global__ void __launch_bounds__(NT) k_gradmax(const float* __restrict__ u, KPa
   }
 }
 
+// Local sums of the discrete energies (Sec. 5.3 / 5.4), FP64, one cell (and
+// its vertex at +1/2 in every axis) per thread, grid-stride:
+//   t0 = sum (u - f)^2 (order 4) or sum u^2 (order 6),
+//   t1 = sum (u - gbar) f (order 6),  t2 = sum (h^2 Delta_h u)^2,
+//   t3 = sum over vertices |G|^p (G = g / q, unscaled vertex gradient),
+// into ctrl->rd, dd, lapdd, tdd.
+__global__ void __launch_bounds__(NT) k_energy_terms(const double* __restrict__ u, const double* __restrict__ f,
+                                                     double gbar, KParams kp, Ctrl* ctrl, double* partials) {
+  __shared__ double sred[32 * 4];
+  __shared__ int sflag;
+  const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+  const int lx = __ffs(nx) - 1, lxy = lx + __ffs(ny) - 1;  // sizes are powers of two
+  const size_t plane = (size_t)nx * ny, n = plane * nz;
+  const bool d3 = kp.dim == 3;
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    const int x = (int)(i & (nx - 1)), y = (int)((i >> lx) & (ny - 1)), z = (int)(i >> lxy);
+    const int xp = (x + 1) & (nx - 1), xm = (x - 1) & (nx - 1), yp = (y + 1) & (ny - 1), ym = (y - 1) & (ny - 1);
+    auto at = [&](int zz, int yy, int xx) { return u[(size_t)zz * plane + (size_t)yy * nx + xx]; };
+    const double c = u[i];
+    const double sum = (at(z, y, xm) + at(z, y, xp)) + (at(z, ym, x) + at(z, yp, x));
+    double lapc = sum - 4.0 * c;
+    if (d3) {
+      const int zp = (z + 1) & (nz - 1), zm = (z - 1) & (nz - 1);
+      lapc = (sum + (at(zm, y, x) + at(zp, y, x))) - 6.0 * c;
+    }
+    t[2] += lapc * lapc;
+    double G2;
+    if (d3) {
+      const int z1 = (z + 1) & (nz - 1);
+      const double u000 = c, u001 = at(z, y, xp), u010 = at(z, yp, x), u011 = at(z, yp, xp);
+      const double u100 = at(z1, y, x), u101 = at(z1, y, xp), u110 = at(z1, yp, x), u111 = at(z1, yp, xp);
+      const double g0 = ((u001 - u000) + (u011 - u010)) + ((u101 - u100) + (u111 - u110));
+      const double g1 = ((u010 - u000) + (u011 - u001)) + ((u110 - u100) + (u111 - u101));
+      const double g2 = ((u100 - u000) + (u101 - u001)) + ((u110 - u010) + (u111 - u011));
+      G2 = g0 * g0 + g1 * g1 + g2 * g2;
+    } else {
+      const double u00 = c, u01 = at(0, y, xp), u10 = at(0, yp, x), u11 = at(0, yp, xp);
+      const double g0 = (u01 - u00) + (u11 - u10), g1 = (u10 - u00) + (u11 - u01);
+      G2 = g0 * g0 + g1 * g1;
+    }
+    t[3] += (kp.p == 4.0) ? G2 * G2 : pow(G2, 0.5 * kp.p);
+    if (kp.order == 4) {
+      const double e = c - f[i];
+      t[0] += e * e;
+    } else {
+      t[0] += c * c;
+      t[1] += (c - gbar) * f[i];
+    }
+  }
+  block_reduce<double, 4, false>(t, sred);
+  if (publish_and_check_last<double>(t, 4, partials, &ctrl->counter[CS_RES], &sflag)) {
+    double tt[4];
+    gather_partials<double, 4, false>(tt, partials, sred);
+    if (threadIdx.x == 0) {
+      ctrl->rd = tt[0];
+      ctrl->dd = tt[1];
+      ctrl->lapdd = tt[2];
+      ctrl->tdd = tt[3];
+      ctrl->counter[CS_RES] = 0;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ misc
 template <typename T>
 __global__ void k_axpby(T* y, const T* x, const T* z, double a, double b, double c, size_t n) {
@@ -860,6 +924,12 @@ cudaError_t launch_dot(const double* x, const double* y, const double* z, size_t
 cudaError_t launch_gradmax(const float* u, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st) {
   const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
   k_gradmax<<<std::min(grid1d(n), 1024), NT, 0, st>>>(u, kp, ctrl, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_energy_terms(const double* u, const double* f, double gbar, const KParams& kp, Ctrl* ctrl,
+                                double* partials, cudaStream_t st) {
+  const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
+  k_energy_terms<<<std::min(grid1d(n), 1024), NT, 0, st>>>(u, f, gbar, kp, ctrl, partials);
   return cudaGetLastError();
 }
 cudaError_t launch_norms(const double* x, size_t n, double hd, Ctrl* c, double* partials, cudaStream_t st) {

@@ -111,6 +111,16 @@ cudaError_t launch_linesearch(const T* u, const T* ubase, const T* d, int pk, co
 // float-float flux of the FP64 residual).  3D grids with nx >= 32, ny >= 8.
 cudaError_t launch_gradmax(const float* u, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st);
 
+// Local sums of the discrete energy of u (FP64) into ctrl->rd, dd, lapdd,
+// tdd: sum (u - f)^2 (order 4) or sum u^2 (order 6); sum (u - gbar) f
+// (order 6); sum (h^2 Delta_h u)^2; sum over vertices |G|^p.
+cudaError_t launch_energy_terms(const double* u, const double* f, double gbar, const KParams& kp, Ctrl* ctrl,
+                                double* partials, cudaStream_t st);
+// sum over the spectrum of a^2 / mu (mu > 0) into ctrl->rd (a: a DHT).
+template <typename T>
+cudaError_t launch_spec_quad(const T* a, const KParams& kp, Ctrl* ctrl, double* partials, const AxisTables<T>& tb,
+                             cudaStream_t st);
+
 // Number of blocks launch_residual<T> uses for this problem size (one
 // partial sum record per block); fp32 = (T is float).
 long long residual_grid_blocks(const KParams& kp, bool fp32);

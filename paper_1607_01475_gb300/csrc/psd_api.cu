@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -115,6 +116,16 @@ psd_status fail(psd_context* c, psd_status s, const std::string& msg) {
 template <typename T>
 psd_status alloc(psd_context* c, T** p, size_t n) {
   if (*p) return PSD_OK;
+  if (c->prm.alloc) {
+    void* q = c->prm.alloc(n * sizeof(T), c->prm.alloc_ctx);
+    if (!q) return fail(c, PSD_ERR_NOMEM, "the allocator callback returned NULL");
+    if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+      c->prm.free_fn(q, c->prm.alloc_ctx);
+      return fail(c, PSD_ERR_NOMEM, "the allocator callback returned memory not aligned to 256 bytes");
+    }
+    *p = static_cast<T*>(q);
+    return PSD_OK;
+  }
   cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -122,6 +133,14 @@ psd_status alloc(psd_context* c, T** p, size_t n) {
     return fail(c, PSD_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
   return PSD_OK;
+}
+
+void dev_free(psd_context* c, void* p) {
+  if (!p) return;
+  if (c->prm.free_fn)
+    c->prm.free_fn(p, c->prm.alloc_ctx);
+  else
+    cudaFree(p);
 }
 
 #define TRY(x)                   \
@@ -151,6 +170,8 @@ psd_status validate(const psd_params* p, std::string& why) {
   if (p->precision == PSD_MIXED && p->max_outer < 1) return why = "max_outer must be >= 1", PSD_ERR_INVALID;
   if (!(p->inner_eta >= 0 && p->inner_eta < 1)) return why = "inner_eta must be in [0, 1)", PSD_ERR_INVALID;
   if (p->inner_stall < 0) return why = "inner_stall must be >= 0", PSD_ERR_INVALID;
+  if ((p->alloc == nullptr) != (p->free_fn == nullptr))
+    return why = "alloc and free_fn must both be set or both be NULL", PSD_ERR_INVALID;
   return PSD_OK;
 }
 
@@ -198,7 +219,11 @@ psd_status build_tables(psd_context* c) {
         const float hi = (float)v;
         hff[offs[a][w] + t] = psd::ff(hi, (float)(v - (long double)hi));
       }
-  CK(cudaMalloc(&c->tables, tot * (sizeof(double) + sizeof(float) + sizeof(psd::ff))));
+  {
+    unsigned char* t = nullptr;
+    TRY(alloc(c, &t, tot * (sizeof(double) + sizeof(float) + sizeof(psd::ff))));
+    c->tables = t;
+  }
   double* d64 = (double*)c->tables;
   psd::ff* dff = (psd::ff*)(d64 + tot);
   float* d32 = (float*)(dff + tot);
@@ -501,6 +526,7 @@ psd_status solve_fp64(psd_context* c, const double* f, const double* g, double* 
     info->outer_iters = 0;
     info->res_l2 = hc.res_l2;
     info->res_linf = hc.res_linf;
+    info->energy = NAN;
     info->last_alpha = hc.alpha;
     info->wall_ms = ms;
     info->status = hc.status;
@@ -632,11 +658,48 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
     info->outer_iters = outer;
     info->res_l2 = res;
     info->res_linf = resinf;
+    info->energy = NAN;
     info->last_alpha = last_alpha;
     info->wall_ms = ms;
     info->status = status;
   }
   return (psd_status)status;
+}
+
+// E_h[u] (Sec. 5.3 / 5.4 discrete energies; order 6 in the u = nu + gbar
+// variables, with 1/2 ||u - g||_{-1}^2 = 1/2 (u - g, T_h[u - g])_2 by
+// Parseval), FP64.  Uses W and ctrl2.
+psd_status compute_energy(psd_context* c, const double* u, const double* f, const double* g, double* out) {
+  const KParams& kp = c->kp;
+  TRY(ensure_fp64(c));
+  double gbar = 0.0;
+  if (kp.order == 6) {
+    Ctrl hg;
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(g, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+    TRY(read_ctrl(c, c->ctrl2, hg));
+    gbar = hg.rd / (double)c->N;
+  }
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_energy_terms(u, f, gbar, kp, c->ctrl2, c->partials, c->st)); }
+  Ctrl t;
+  TRY(read_ctrl(c, c->ctrl2, t));
+  const double h2 = kp.h * kp.h;
+  double E = kp.s / kp.p * kp.hd * std::pow(kp.q, kp.p) * t.tdd + 0.5 * kp.s * kp.eps2 * kp.hd * t.lapdd / (h2 * h2);
+  if (kp.order == 4) {
+    E += 0.5 * kp.hd * t.rd;
+  } else {
+    E += 0.5 * kp.lam * kp.s * kp.hd * t.rd - kp.hd * t.dd;
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->W, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
+    TRY(full_dht<double>(c, c->W, 1.0, c->tb64));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec_quad<double>(c->W, kp, c->ctrl2, c->partials, c->tb64, c->st)); }
+    Ctrl q;
+    TRY(read_ctrl(c, c->ctrl2, q));
+    E += 0.5 * kp.hd * q.rd * kp.inv_ntot;
+  }
+  *out = E;
+  return PSD_OK;
 }
 
 }  // namespace
@@ -727,8 +790,7 @@ psd_status psd_destroy(psd_handle c) {
   if (!c) return PSD_OK;
   void* ptrs[] = {c->tables, c->ub, c->W, c->D, c->Z, c->Dsp, c->u32, c->da, c->db, c->W32, c->D32,
                   c->R32, c->Dsp32, c->partials, c->ctrl, c->ctrl2, c->d_hist};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dev_free(c, p);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -807,7 +869,7 @@ psd_status psd_set_history(psd_handle c, double* alpha_hist, double* res_hist, i
   if (!c) return PSD_ERR_INVALID;
   if (cap < 0) return fail(c, PSD_ERR_INVALID, "cap must be >= 0");
   if (c->d_hist) {
-    cudaFree(c->d_hist);
+    dev_free(c, c->d_hist);
     c->d_hist = nullptr;
   }
   c->hist_cap = 0;
@@ -990,6 +1052,7 @@ psd_status psd_adjoint(psd_handle c, const double* u, const double* grad_u, doub
     info->outer_iters = 0;
     info->res_l2 = rel;
     info->res_linf = -1.0;
+    info->energy = NAN;
     info->last_alpha = 0.0;
     info->wall_ms = ms;
     info->status = status;
@@ -1026,9 +1089,17 @@ psd_status psd_solve(psd_handle c, const double* f, const double* g, double* u, 
     { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(w, w, nullptr, -1.0, 0.0, kp.s * kp.lam * gbar - fbar, c->N, c->st)); }
     CK(cudaStreamSynchronize(c->st));
   }
+  if (c->prm.report_energy && info) TRY(compute_energy(c, u, f, g, &info->energy));
   if (s != PSD_OK)
     fail(c, s, std::string("solve ended with ") + psd_status_string(s));
   return s;
+}
+
+psd_status psd_energy(psd_handle c, const double* u, const double* f, const double* g, double* energy) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u || !f || !energy) return fail(c, PSD_ERR_INVALID, "u, f and energy are required");
+  if (c->prm.order == 6 && !g) return fail(c, PSD_ERR_INVALID, "order 6 requires g");
+  return compute_energy(c, u, f, g, energy);
 }
 
 }  // extern "C"

@@ -56,12 +56,18 @@ def _params(**kw):
     dict(dim=3, n=(ctypes.c_int * 3)(8, 8, 8), p=7.0), dict(s=-1.0), dict(eps=0.0),
     dict(lam=-1.0), dict(precision=3), dict(tol=-1.0), dict(max_iter=-1),
     dict(precision=1, max_outer=0), dict(inner_eta=1.0), dict(inner_eta=-0.5), dict(inner_stall=-1),
+    "alloc_without_free",
 ])
 def test_create_rejects_invalid_parameters(lib, bad):
     """Invalid parameters are refused with PSD_ERR_INVALID before any device
     work (so this runs without a GPU)."""
     out = ctypes.c_void_p()
-    prm = _params(**bad)
+    if bad == "alloc_without_free":
+        from paper_1607_01475_gb300._lib import ALLOC_FN
+        keep = ALLOC_FN(lambda n, ctx: 0)
+        prm = _params(alloc=keep)
+    else:
+        prm = _params(**bad)
     assert lib.psd_create(ctypes.byref(prm), ctypes.byref(out)) == 1
     assert not out.value
     buf = ctypes.create_string_buffer(256)
