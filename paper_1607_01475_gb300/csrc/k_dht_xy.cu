@@ -112,13 +112,20 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(XY<N>::THREAD
   cluster.sync();  // no CTA leaves while another may still read its row block
 }
 
+// The kernel's shared-memory limit, set once per process (thread-safe; first
+// reached from psd_create, so never inside a stream capture).
+template <int N>
+cudaError_t xy_attr() {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_dht_xy<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XY<N>::SMEM);
+  return attr;
+}
+
 template <int N>
 cudaError_t xy_impl(const float* src, float* dst, int nz, const int* done, const AxisTables<float>& tb,
                     cudaStream_t st) {
   using C = XY<N>;
-  // once per process, thread-safe (batched solves launch from several threads)
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(k_dht_xy<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  const cudaError_t attr = xy_attr<N>();
   if (attr != cudaSuccess) return attr;
   dim3 grid(kCluster, nz);
   k_dht_xy<N><<<grid, C::THREADS, C::SMEM, st>>>(src, dst, done, tb.twc[0], tb.tws[0], tb.twc[1], tb.tws[1]);
@@ -129,6 +136,15 @@ cudaError_t xy_impl(const float* src, float* dst, int nz, const int* done, const
 
 bool dht_xy_supported(const KParams& kp) {
   return kp.dim == 3 && kp.nx == kp.ny && (kp.nx == 64 || kp.nx == 128 || kp.nx == 256);
+}
+
+cudaError_t prepare_dht_xy(const KParams& kp) {
+  if (!dht_xy_supported(kp)) return cudaSuccess;
+  switch (kp.nx) {
+    case 64: return xy_attr<64>();
+    case 128: return xy_attr<128>();
+    default: return xy_attr<256>();
+  }
 }
 
 cudaError_t launch_dht_xy(const float* src, float* dst, const KParams& kp, const int* done,

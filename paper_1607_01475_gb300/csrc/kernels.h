@@ -47,6 +47,7 @@ cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, cons
 // {64, 128, 256}; one thread-block cluster per plane), src -> dst (may
 // alias).  Skipped when *done != 0.
 bool dht_xy_supported(const KParams& kp);
+cudaError_t prepare_dht_xy(const KParams& kp);  // one-time kernel attributes (call outside any capture)
 cudaError_t launch_dht_xy(const float* src, float* dst, const KParams& kp, const int* done,
                           const AxisTables<float>& tb, cudaStream_t st);
 

@@ -33,6 +33,7 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr int kChunk = 8;          // iterations enqueued between host checks
+static_assert(kChunk % 2 == 0, "a chunk must start and end on the same ping-pong parity");
 constexpr int kLsPassesGen = 16;   // Newton passes of the general-p line search
 constexpr double kInnerEta = 1e-4;  // inner FP32 solve: relative drop of the preconditioned norm
 constexpr int kInnerStall = 5;      // ... or this many iterations without halving it
@@ -94,6 +95,15 @@ struct psd_context {
   double prof_ms[PSD_PROF_CLASSES] = {};
   long long prof_n[PSD_PROF_CLASSES] = {};
   std::vector<float> prof_durs[PSD_PROF_CLASSES];  // per-launch durations (ms)
+
+  // CUDA graphs of one chunk of iterations, captured on a private stream and
+  // replayed on st: the mixed inner chunk (all arguments are the handle's
+  // own buffers) and the FP64 chunk (keyed on the caller's u, f, g)
+  cudaStream_t gst = nullptr;
+  cudaGraphExec_t g_inner = nullptr;
+  cudaGraphExec_t g_fp64 = nullptr;
+  const void* g_fp64_key[3] = {nullptr, nullptr, nullptr};
+  bool graphs_off = false;  // a capture failed once: launch directly from then on
 };
 
 namespace {
@@ -289,6 +299,41 @@ struct ProfScope {
     if (cudaEventRecord(c->ev_pool[a + 1], c->st) == cudaSuccess) c->recs.push_back({cls, a, a + 1});
   }
 };
+
+// Enqueue one chunk of iterations through a cached CUDA graph (captured the
+// first time on the private stream and launched on st, whose stream order
+// then places it after the work queued before), or directly while tracing
+// is on or after a failed capture.
+template <typename Enq>
+psd_status run_chunk(psd_context* c, cudaGraphExec_t* cache, Enq&& enqueue) {
+  if (c->prof || c->graphs_off) return enqueue();
+  if (!*cache) {
+    if (!c->gst && cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      c->graphs_off = true;
+      return enqueue();
+    }
+    cudaStream_t saved = c->st;
+    c->st = c->gst;
+    cudaGraph_t g = nullptr;
+    psd_status s = PSD_OK;
+    if (cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      s = enqueue();
+      if (cudaStreamEndCapture(c->gst, &g) != cudaSuccess) g = nullptr;
+    }
+    c->st = saved;
+    if (s != PSD_OK || g == nullptr || cudaGraphInstantiate(cache, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      *cache = nullptr;
+      c->graphs_off = true;
+      return enqueue();
+    }
+    cudaGraphDestroy(g);
+  }
+  CK(cudaGraphLaunch(*cache, c->st));
+  return PSD_OK;
+}
 
 template <typename T>
 constexpr int cls_of(int fp64cls) {
@@ -500,15 +545,29 @@ psd_status solve_fp64(psd_context* c, const double* f, const double* g, double* 
   }
   int k = 0;
   Ctrl hc;
-  for (;;) {
-    for (int i = 0; i < kChunk; ++i, ++k) {
-      double* cur = (k % 2 == 0) ? u : c->ub;
-      double* nxt = (k % 2 == 0) ? c->ub : u;
+  // a chunk always starts at an even k (kChunk is even), so one graph serves
+  // every chunk
+  auto chunk = [&]() -> psd_status {
+    for (int i = 0; i < kChunk; ++i) {
+      double* cur = (i % 2 == 0) ? u : c->ub;
+      double* nxt = (i % 2 == 0) ? c->ub : u;
       TRY(precond_passes<double>(c, c->W, c->D, c->ctrl, c->Z, c->Dsp, c->tb64));
       TRY(linesearch<double>(c, cur, nullptr, c->D, c->ctrl));
       ResArgs<double> a{cur, c->D, nxt, f, nullptr, c->W, kp.order == 4 ? 1 : 0, 1};
       { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl, c->partials, c->st)); }
     }
+    return PSD_OK;
+  };
+  if (c->g_fp64 && (c->g_fp64_key[0] != u || c->g_fp64_key[1] != f || c->g_fp64_key[2] != g)) {
+    cudaGraphExecDestroy(c->g_fp64);
+    c->g_fp64 = nullptr;
+  }
+  c->g_fp64_key[0] = u;
+  c->g_fp64_key[1] = f;
+  c->g_fp64_key[2] = g;
+  for (;;) {
+    TRY(run_chunk(c, &c->g_fp64, chunk));
+    k += kChunk;
     TRY(read_ctrl(c, c->ctrl, hc));
     if (hc.done) break;
     if (k > c->prm.max_iter + 2 * kChunk) {  // host-side guard: never loop unbounded
@@ -627,15 +686,20 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
     }
     int k = 0;
     Ctrl hc;
-    for (;;) {
-      for (int i = 0; i < kChunk; ++i, ++k) {
-        float* cur = (k % 2 == 0) ? c->da : c->db;
-        float* nxt = (k % 2 == 0) ? c->db : c->da;
+    auto chunk = [&]() -> psd_status {
+      for (int i = 0; i < kChunk; ++i) {
+        float* cur = (i % 2 == 0) ? c->da : c->db;
+        float* nxt = (i % 2 == 0) ? c->db : c->da;
         TRY(precond_passes<float>(c, c->W32, c->D32, c->ctrl, six ? c->R32 : nullptr, c->Dsp32, c->tb32));
         TRY(linesearch<float>(c, cur, c->u32, c->D32, c->ctrl));
         ResArgs<float> a{cur, c->D32, nxt, rphys, c->u32, c->W32, norm, 1};
         { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_INNER, c->pk, kp, c->ctrl, c->partials, c->st)); }
       }
+      return PSD_OK;
+    };
+    for (;;) {
+      TRY(run_chunk(c, &c->g_inner, chunk));
+      k += kChunk;
       TRY(read_ctrl(c, c->ctrl, hc));
       if (hc.done) break;
       if (k > h.max_iter + 2 * kChunk) break;  // host-side guard
@@ -757,6 +821,13 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
   c->pk = (params->p == 4.0) ? psd::PK_4 : psd::PK_GEN;
   static const bool attrs = (psd::init_dht_attributes(), true);  // once, thread-safe
   (void)attrs;
+  if (psd::prepare_dht_xy(kp) != cudaSuccess) {
+    cudaGetLastError();
+    c->err = "cudaFuncSetAttribute failed for the cluster transform";
+    g_create_error = c->err;
+    psd_destroy(c);
+    return PSD_ERR_CUDA;
+  }
   auto bail = [&](psd_status st) {
     g_create_error = c->err;
     psd_destroy(c);
@@ -792,6 +863,9 @@ psd_status psd_destroy(psd_handle c) {
                   c->R32, c->Dsp32, c->partials, c->ctrl, c->ctrl2, c->d_hist};
   for (void* p : ptrs) dev_free(c, p);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->g_inner) cudaGraphExecDestroy(c->g_inner);
+  if (c->g_fp64) cudaGraphExecDestroy(c->g_fp64);
+  if (c->gst) cudaStreamDestroy(c->gst);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
