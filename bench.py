@@ -107,7 +107,7 @@ class ClockSampler:
 # sixth-order path (reads + writes of whole fields, in the class precision).
 CLASS_NAMES = ["residual_fp64", "residual_fp32", "dht_rows_fp64", "dht_rows_fp32", "dht_cols_fp64",
                "dht_cols_fp32", "mid_fp64", "mid_fp32", "linesearch_fp64", "linesearch_fp32", "other",
-               "dht_rows_ff", "dht_cols_ff", "dht_xy_fp32"]
+               "dht_rows_ff", "dht_cols_ff"]
 
 
 def algorithmic_bytes_per_cell(cls, order):
@@ -116,7 +116,7 @@ def algorithmic_bytes_per_cell(cls, order):
     table = {
         # inner (order 6): delta, d, ubase in; delta', r out.  FP64 plain: u, d, f in; u', r out
         "residual": (5 if order == 6 else 6) if fp32 else 5,
-        "dht_rows": 2, "dht_cols": 2, "dht_xy": 2,
+        "dht_rows": 2, "dht_cols": 2,
         # order 6: the line W, xi and dspec each read and written once
         "mid": 6 if order == 6 else 2,
         "linesearch": 3 if fp32 else 2,  # delta, ubase, d  /  u, d

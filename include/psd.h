@@ -128,8 +128,7 @@ psd_status psd_energy(psd_handle h, const double* u, const double* f,
 psd_status psd_precond_solve(psd_handle h, const double* r, double* d);
 
 /* The same solve in FP32 with the kernels of the mixed solver's inner
- * iteration (for 3D grids with nx = ny in {64, 128, 256} the fused x/y
- * cluster pass).  r, d: float32 device grids; may alias.  Asynchronous.    */
+ * iteration.  r, d: float32 device grids; may alias.  Asynchronous.        */
 psd_status psd_precond_solve_f32(psd_handle h, const float* r, float* d);
 
 /* PSD solve of N_h[u] = f (order 6: with g) from the initial guess in u; u
@@ -183,8 +182,7 @@ enum {
   PSD_PROF_LINESEARCH_FP64 = 8, PSD_PROF_LINESEARCH_FP32 = 9,
   PSD_PROF_OTHER = 10,
   PSD_PROF_DHT_ROWS_FF = 11,  PSD_PROF_DHT_COLS_FF = 12,  /* float-float passes */
-  PSD_PROF_DHT_XY_FP32 = 13,  /* fused x and y passes                         */
-  PSD_PROF_CLASSES = 14
+  PSD_PROF_CLASSES = 13
 };
 
 /* Per-kernel timing (tracing).  While enabled, every kernel launch of this

@@ -13,7 +13,7 @@ _LIB_NAME = "libpsd.so"
 
 PSD_FP64 = 0
 PSD_MIXED = 1
-PSD_PROF_CLASSES = 14  # kernel classes of psd_profile_read
+PSD_PROF_CLASSES = 13  # kernel classes of psd_profile_read
 
 _STATUS = {0: "PSD_OK", 1: "PSD_ERR_INVALID", 2: "PSD_ERR_NOMEM", 3: "PSD_ERR_CUDA",
            4: "PSD_ERR_NOCONV", 5: "PSD_ERR_TIMEOUT", 6: "PSD_ERR_UNSUPPORTED",

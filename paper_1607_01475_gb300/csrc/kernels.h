@@ -43,14 +43,6 @@ cudaError_t launch_dht_cols_ff(ff* data, const KParams& kp, int ax, const AxisTa
 cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
                                double* partials, const AxisTables<ff>& tb, cudaStream_t st);
 
-// x and y passes of every z-plane fused in one kernel (FP32, 3D, nx = ny in
-// {64, 128, 256}; one thread-block cluster per plane), src -> dst (may
-// alias).  Skipped when *done != 0.
-bool dht_xy_supported(const KParams& kp);
-cudaError_t prepare_dht_xy(const KParams& kp);  // one-time kernel attributes (call outside any capture)
-cudaError_t launch_dht_xy(const float* src, float* dst, const KParams& kp, const int* done,
-                          const AxisTables<float>& tb, cudaStream_t st);
-
 // The middle pass along the slowest axis (y in 2D, z in 3D) of the
 // preconditioner: forward DHT, division by the symbol of L_h, Parseval sums
 // into ctrl, inverse DHT (with the 1/N of the whole transform).  Order 6

@@ -403,15 +403,6 @@ psd_status precond_passes(psd_context* c, T* W, T* D, Ctrl* ctrl, T* xi, T* dspe
   const KParams& kp = c->kp;
   const int* done = &ctrl->done;
   const int nrows = kp.ny * kp.nz;
-  if constexpr (sizeof(T) == 4) {
-    if (psd::dht_xy_supported(kp)) {
-      // forward x, y in one cluster kernel; z, symbol and inverse z; inverse x, y
-      { ProfScope p_(c, PSD_PROF_DHT_XY_FP32); CK(psd::launch_dht_xy(W, W, kp, done, tb, c->st)); }
-      { ProfScope p_(c, PSD_PROF_MID_FP32); CK(psd::launch_mid<T>(W, kp, ctrl, c->partials, xi, dspec, tb, c->st)); }
-      { ProfScope p_(c, PSD_PROF_DHT_XY_FP32); CK(psd::launch_dht_xy(W, D, kp, done, tb, c->st)); }
-      return PSD_OK;
-    }
-  }
   { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_ROWS_FP64)); CK(psd::launch_dht_rows<T>(W, W, kp.nx, nrows, T(1), done, tb, c->st)); }
   if (kp.dim == 3) { ProfScope p_(c, cls_of<T>(PSD_PROF_DHT_COLS_FP64)); CK(psd::launch_dht_cols<T>(W, kp, 1, T(1), done, tb, c->st)); }
   { ProfScope p_(c, cls_of<T>(PSD_PROF_MID_FP64)); CK(psd::launch_mid<T>(W, kp, ctrl, c->partials, xi, dspec, tb, c->st)); }
@@ -821,13 +812,7 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
   c->pk = (params->p == 4.0) ? psd::PK_4 : psd::PK_GEN;
   static const bool attrs = (psd::init_dht_attributes(), true);  // once, thread-safe
   (void)attrs;
-  if (psd::prepare_dht_xy(kp) != cudaSuccess) {
-    cudaGetLastError();
-    c->err = "cudaFuncSetAttribute failed for the cluster transform";
-    g_create_error = c->err;
-    psd_destroy(c);
-    return PSD_ERR_CUDA;
-  }
+
   auto bail = [&](psd_status st) {
     g_create_error = c->err;
     psd_destroy(c);
@@ -928,7 +913,7 @@ const char* psd_profile_class_name(int k) {
   static const char* names[PSD_PROF_CLASSES] = {
       "residual_fp64", "residual_fp32", "dht_rows_fp64", "dht_rows_fp32", "dht_cols_fp64", "dht_cols_fp32",
       "mid_fp64",      "mid_fp32",      "linesearch_fp64", "linesearch_fp32", "other",
-      "dht_rows_ff",   "dht_cols_ff",   "dht_xy_fp32"};
+      "dht_rows_ff",   "dht_cols_ff"};
   return (k >= 0 && k < PSD_PROF_CLASSES) ? names[k] : nullptr;
 }
 

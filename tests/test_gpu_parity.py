@@ -133,9 +133,7 @@ def test_mixed_solve_register_blocked(p):
 @pytest.mark.parametrize("shape", [(32, 64, 64), (16, 128, 128), (8, 256, 256), (16, 32, 64), (64, 64)])
 @pytest.mark.parametrize("order", [4, 6])
 def test_precond_f32_parity(oracle, shape, order):
-    """The FP32 preconditioner of the inner solve (the fused x/y cluster
-    pass for nx = ny in {64, 128, 256}, separate passes otherwise) against
-    the FP64 oracle.  FP32 transform rounding is ~log2(N) eps32 of the
+    """The FP32 preconditioner of the inner solve against the FP64 oracle.  FP32 transform rounding is ~log2(N) eps32 of the
     input's norm; a smooth input keeps d = L_h^{-1} r of the same size as r
     (for white noise d is ~1e-2 of r and the bound would be ~1e-4)."""
     P, h = _problem(oracle, order, shape, 4.0)
