@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kThreads)
     k_dht_last_ff(const ff* data, double* theta, float* out32, size_t line_stride, size_t outer_stride,
                   KParams kp, Ctrl* ctrl, double* partials, const ff* __restrict__ twc,
                   const ff* __restrict__ tws, const ff* __restrict__ symx, const ff* __restrict__ symo,
-                  const ff* __restrict__ syml) {
+                  const ff* __restrict__ syml, double* dc) {
   using T = ff;
   using F = LineFFT<T, N, RM>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(kThreads)
       const ff mu = ff_add(mx[c], ml);
       const bool live = mu.hi > 0.0f;
       if (EPI == EPI_THETA) {
+        if (dc != nullptr && c == 0 && x == 0 && blockIdx.y == 0 && k == 0) *dc = ff_to_double_bits(h[0]);
         const ff t = live ? ff_mul(h[c], ff_recip(mu)) : ff(0.0f, 0.0f);
         outv[c] = ff_to_double_bits(ff_add(ff_from_double_bits(thv[c]), t));
       } else {
@@ -664,7 +665,7 @@ cudaError_t launch_dht_rows_ff_from_f32(const float* src, ff* dst, int nx, int n
 
 template <int N>
 cudaError_t last_ff_impl(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
-                         double* partials, const AxisTables<ff>& tb, cudaStream_t st) {
+                         double* partials, const AxisTables<ff>& tb, cudaStream_t st, double* dc) {
   constexpr int RM = radix_pass<ff>();
   using F = LineFFT<ff, N, RM>;
   const int nx = kp.nx;
@@ -681,18 +682,18 @@ cudaError_t last_ff_impl(const ff* data, double* theta, float* out32, const KPar
   if (out32 == nullptr)
     k_dht_last_ff<N, RM, EPI_THETA><<<grid, pairs * F::TS, sm, st>>>(data, theta, out32, line_stride, outer_stride,
                                                                     kp, ctrl, partials, tb.twc[ax], tb.tws[ax],
-                                                                    tb.sym[0], symo, tb.sym[ax]);
+                                                                    tb.sym[0], symo, tb.sym[ax], dc);
   else
     k_dht_last_ff<N, RM, EPI_RESID><<<grid, pairs * F::TS, sm, st>>>(data, theta, out32, line_stride, outer_stride,
                                                                     kp, ctrl, partials, tb.twc[ax], tb.tws[ax],
-                                                                    tb.sym[0], symo, tb.sym[ax]);
+                                                                    tb.sym[0], symo, tb.sym[ax], nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
-                               double* partials, const AxisTables<ff>& tb, cudaStream_t st) {
+                               double* partials, const AxisTables<ff>& tb, cudaStream_t st, double* dc) {
   const int n = kp.dim == 3 ? kp.nz : kp.ny;
-  PSD_DISPATCH_N(n, (last_ff_impl<NN>(data, theta, out32, kp, ctrl, partials, tb, st)));
+  PSD_DISPATCH_N(n, (last_ff_impl<NN>(data, theta, out32, kp, ctrl, partials, tb, st, dc)));
 }
 
 template <typename T>

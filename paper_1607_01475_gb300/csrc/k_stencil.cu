@@ -762,9 +762,10 @@ __global__ void k_round_f32(float* out, const double* in, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
 }
-__global__ void k_accumulate_f64(double* u, const float* delta, float* u32, size_t n) {
+__global__ void k_accumulate_f64(double* u, const float* delta, float* u32, size_t n, const double* dsum) {
+  const double m = dsum ? *dsum / (double)n : 0.0;  // mean of delta, removed
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = u[i] + (double)delta[i];
+    const double v = u[i] + ((double)delta[i] - m);
     u[i] = v;
     u32[i] = (float)v;
   }
@@ -940,8 +941,9 @@ cudaError_t launch_round_f32(float* out, const double* in, size_t n, cudaStream_
   k_round_f32<<<grid1d(n), 256, 0, st>>>(out, in, n);
   return cudaGetLastError();
 }
-cudaError_t launch_accumulate_f64(double* u, const float* delta, float* u32, size_t n, cudaStream_t st) {
-  k_accumulate_f64<<<grid1d(n), 256, 0, st>>>(u, delta, u32, n);
+cudaError_t launch_accumulate_f64(double* u, const float* delta, float* u32, size_t n, const double* dsum,
+                                  cudaStream_t st) {
+  k_accumulate_f64<<<grid1d(n), 256, 0, st>>>(u, delta, u32, n, dsum);
   return cudaGetLastError();
 }
 

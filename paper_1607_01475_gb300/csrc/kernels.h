@@ -38,10 +38,12 @@ cudaError_t launch_dht_rows_ff_from_f32(const float* src, ff* dst, int nx, int n
                                         cudaStream_t st);
 cudaError_t launch_dht_cols_ff(ff* data, const KParams& kp, int ax, const AxisTables<ff>& tb, cudaStream_t st);
 // The last pass (z in 3D, y in 2D) with a fused epilogue: out32 == nullptr:
-// theta += DHT(data) / mu; else out32 = (float)(DHT(data) - theta) and
-// ctrl->res_l2 = its Parseval norm (h^d / N sum)^{1/2}.  mu = 0 gives 0.
+// theta += DHT(data) / mu, and (dc != null) *dc = the zero-frequency
+// coefficient (the sum of the transformed field); else out32 = (float)(DHT(data)
+// - theta) and ctrl->res_l2 = its Parseval norm (h^d / N sum)^{1/2}.  mu = 0
+// gives 0.
 cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
-                               double* partials, const AxisTables<ff>& tb, cudaStream_t st);
+                               double* partials, const AxisTables<ff>& tb, cudaStream_t st, double* dc = nullptr);
 
 // The middle pass along the slowest axis (y in 2D, z in 3D) of the
 // preconditioner: forward DHT, division by the symbol of L_h, Parseval sums
@@ -129,7 +131,10 @@ cudaError_t launch_dot(const double* x, const double* y, const double* z, size_t
 cudaError_t launch_norms(const double* x, size_t n, double hd, Ctrl* c, double* partials, cudaStream_t st);
 // out = (float) in;  u += delta, u32 = (float) u  (mixed precision bookkeeping)
 cudaError_t launch_round_f32(float* out, const double* in, size_t n, cudaStream_t st);
-cudaError_t launch_accumulate_f64(double* u, const float* delta, float* u32, size_t n, cudaStream_t st);
+// u += delta - mean(delta) (dsum: device pointer to sum(delta), or null for
+// no mean removal), u32 = (float) u.
+cudaError_t launch_accumulate_f64(double* u, const float* delta, float* u32, size_t n, const double* dsum,
+                                  cudaStream_t st);
 
 void init_dht_attributes();
 

@@ -381,7 +381,7 @@ psd_status full_dht(psd_context* c, T* x, T scale, const AxisTables<T>& tb) {
 
 // theta += DHT(v) / mu (order 6, mixed): v is src64 (FP64, transformed in
 // place) or src32 (FP32, transformed into D); theta lives in Z.
-psd_status dht_theta_ff(psd_context* c, const double* src64, const float* src32) {
+psd_status dht_theta_ff(psd_context* c, const double* src64, const float* src32, double* dc = nullptr) {
   const KParams& kp = c->kp;
   const int nrows = kp.ny * kp.nz;
   psd::ff* x = reinterpret_cast<psd::ff*>(c->D);  // float-float pairs between the passes
@@ -393,7 +393,7 @@ psd_status dht_theta_ff(psd_context* c, const double* src64, const float* src32)
     CK(psd::launch_dht_rows_ff(src64, x, kp.nx, nrows, c->tbff, c->st));
   }
   if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, c->tbff, c->st)); }
-  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(x, c->Z, nullptr, kp, nullptr, c->partials, c->tbff, c->st)); }
+  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(x, c->Z, nullptr, kp, nullptr, c->partials, c->tbff, c->st, dc)); }
   return PSD_OK;
 }
 
@@ -594,12 +594,18 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
   const KParams& kp = c->kp;
   const bool six = kp.order == 6;
   CK(cudaEventRecord(c->ev0, c->st));
-  double gbar = 0.0;
   if (six) {
-    Ctrl hg;
+    // the sixth-order problem lives on mean(u) = mean(g): project u0 once
+    Ctrl hg, hu;
     { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(g, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
     TRY(read_ctrl(c, c->ctrl2, hg));
-    gbar = hg.rd / (double)c->N;
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+    TRY(read_ctrl(c, c->ctrl2, hu));
+    const double shift = (hg.rd - hu.rd) / (double)c->N;
+    if (shift != 0.0) {
+      ProfScope p_(c, PSD_PROF_OTHER);
+      CK(psd::launch_axpby<double>(u, u, nullptr, 1.0, 0.0, shift, c->N, c->st));
+    }
   }
   { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
   if (six) {
@@ -614,17 +620,13 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
   const float* delta = nullptr;
   for (;;) {
     if (delta) {
-      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, delta, c->u32, c->N, c->st)); }
-      if (six) {
-        TRY(dht_theta_ff(c, nullptr, delta));  // theta += DHT(T_h delta)
-        // keep mean(u) = mean(g) exactly: delta is mean-zero only up to FP32 rounding
-        Ctrl hu;
-        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
-        TRY(read_ctrl(c, c->ctrl2, hu));
-        const double shift = gbar - hu.rd / (double)c->N;
-        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(u, u, nullptr, 1.0, 0.0, shift, c->N, c->st)); }
-        { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
-      }
+      // order 6: theta += DHT(T_h delta); the zero-frequency coefficient of the
+      // transform, sum(delta), is recorded on the device and the accumulation
+      // removes the mean of delta, which is zero only up to FP32 rounding,
+      // so that mean(u) = mean(g) holds throughout
+      double* dsum = six ? &c->ctrl2->c3 : nullptr;
+      if (six) TRY(dht_theta_ff(c, nullptr, delta, dsum));
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, delta, c->u32, c->N, dsum, c->st)); }
     }
     bool fluxff = false;
     TRY(use_fluxff(c, &fluxff));
