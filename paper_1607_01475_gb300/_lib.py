@@ -39,6 +39,9 @@ class PSDInfo(ctypes.Structure):
                 ("res_linf", ctypes.c_double), ("energy", ctypes.c_double), ("last_alpha", ctypes.c_double),
                 ("wall_ms", ctypes.c_double), ("status", ctypes.c_int)]
 
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
 
 # ctypes callback objects must outlive the handle that calls them
 _callbacks = {}
@@ -50,9 +53,6 @@ def _allocator_callbacks(allocator):
         return ALLOC_FN(), FREE_FN()
     a, f = allocator
     return ALLOC_FN(lambda n, ctx: a(n)), FREE_FN(lambda ptr, ctx: f(ptr))
-
-    def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PSDError(RuntimeError):

@@ -81,3 +81,20 @@ def test_null_arguments(lib):
     assert lib.psd_solve(None, None, None, None, None, None) == 1
     assert lib.psd_residual(None, None, None, None, None, None, None) == 1
     assert lib.psd_precond_solve(None, None, None) == 1
+
+
+def test_info_and_params_structs_match_the_header():
+    """The ctypes mirrors of psd_info and psd_params: field order as in
+    include/psd.h, and the info dict the Python API returns."""
+    import re
+    from paper_1607_01475_gb300._lib import PSDInfo, PSDParams
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "psd.h")).read()
+    for cls, name in ((PSDInfo, "psd_info"), (PSDParams, "psd_params")):
+        body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), hdr, re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = re.findall(r"(\w+)\s*(?:\[\d+\])?\s*;|\(\*(\w+)\)", body)
+        names = [a or b for a, b in fields]
+        py = [("lambda" if f == "lam" else f) for f, _ in cls._fields_]
+        assert names == py, (name, names, py)
+    d = PSDInfo(iters=3, status=0).as_dict()
+    assert d["iters"] == 3 and "energy" in d and "wall_ms" in d
