@@ -12,6 +12,7 @@
 // of u (5, halo 2 in x/y), of Delta_h u (3, halo 1) and of the vertex fluxes
 // (2 vertex planes) in shared memory.  Every vertex flux and every Laplacian
 // value is computed once per CTA.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -817,13 +818,13 @@ ResGeom res_geometry(const KParams& kp, bool fp32) {
     return g;
   }
   if (fp32 && kp.nx % 32 == 0 && kp.ny % 32 == 0 && kp.nz >= 16 &&
-      (long long)(kp.nx / 32) * (kp.ny / 32) * (kp.nz / 16) >= 2 * 152) {
-    const int gx = kp.nx / 32, gy = kp.ny / 32;
-    int zc = kp.nz;  // marches of at least 16 planes; about three CTAs per SM
-    while (zc > 16 && (long long)gx * gy * (kp.nz / zc) < 3 * 152) zc >>= 1;
+      (long long)(kp.nx / 32) * (kp.ny / 32) * (kp.nz / 16) >= 2 * 152 &&
+      (long long)(kp.nx / 32) * (kp.ny / 32) * kp.nz < (1LL << 31)) {
+    // one wave of CTAs sized at launch (rb_wave); grid holds the number of
+    // column-planes, the most CTAs a launch can use
     g.kind = RK_RB4;
-    g.grid = dim3(gx, gy, kp.nz / zc);
-    g.zc = zc;
+    g.grid = dim3((unsigned)((kp.nx / 32) * (kp.ny / 32) * kp.nz));
+    g.zc = 0;
     return g;
   }
   const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY3 ? kp.ny : BY3;
@@ -834,12 +835,24 @@ ResGeom res_geometry(const KParams& kp, bool fp32) {
   return g;
 }
 
+// CTAs of one full wave of a register-blocked kernel: the CTAs per SM that
+// its __launch_bounds__ guarantee (registers; the static shared memory of
+// that many CTAs fits an SM) times the SMs, at most `limit` (the column-planes).
+// Fixed per device, so the partial sums, and the results, do not depend on
+// whether a launch is captured into a graph.
+inline unsigned rb_wave(const KParams& kp, int ctas_per_sm, unsigned limit) {
+  return std::min<unsigned>((unsigned)(ctas_per_sm * kp.nsm), limit);
+}
+
 template <typename T, int PK, int MODE>
 cudaError_t res_impl(const ResArgs<T>& a, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st) {
   const ResGeom g = res_geometry(kp, sizeof(T) == 4);
   switch (g.kind) {
     case RK_RB4:
-      if constexpr (sizeof(T) == 4) k_res3d_rb<T, PK, MODE, 4><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
+      if constexpr (sizeof(T) == 4) {
+        const unsigned nb = rb_wave(kp, 2, g.grid.x);  // __launch_bounds__(256, 2)
+        k_res3d_rb<T, PK, MODE, 4><<<nb, NT, 0, st>>>(a, kp, ctrl, partials);
+      }
       break;
     case RK_COL:
       if constexpr (sizeof(T) == 8 && MODE == RM_PLAIN && PK == PK_4) {
@@ -865,7 +878,10 @@ cudaError_t ls_impl(const T* u, const T* ubase, const T* d, const KParams& kp, C
   const ResGeom g = res_geometry(kp, sizeof(T) == 4);  // the same tiles as the residual
   switch (g.kind) {
     case RK_RB4:
-      if constexpr (sizeof(T) == 4) k_ls3d_rb<T, PK, INNER, 4><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, g.zc);
+      if constexpr (sizeof(T) == 4) {
+        const unsigned nb = rb_wave(kp, 3, g.grid.x);  // __launch_bounds__(256, 3)
+        k_ls3d_rb<T, PK, INNER, 4><<<nb, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials);
+      }
       break;
     case RK_COL:
       k_ls3d_col<T, PK, INNER><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, g.zc);

@@ -71,7 +71,7 @@ struct KParams {
   double hd;            // h^d (cell volume)
   double inv_ntot;      // 1 / (nx ny nz)
   int order;
-  int pad_;
+  int nsm;              // SMs of the current device (finish_kparams; sizes one-wave grids)
   // derived constants (set by finish_kparams): the column kernels work with
   // unscaled vertex-gradient sums G = g / q and Laplacian sums h^2 Delta_h.
   double q;             // 1 / (2^(d-1) h): g = q G
@@ -94,6 +94,11 @@ __device__ __forceinline__ const KConst<float>& kconst<float>(const KParams& kp)
 
 // Fill the derived constants of KParams (host side).
 inline void finish_kparams(KParams& kp) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0)
+    sms = 152;
+  kp.nsm = sms;
   kp.q = kp.inv_h / (kp.dim == 3 ? 4.0 : 2.0);
   const double qp = (kp.p == 4.0) ? kp.q * kp.q * kp.q * kp.q : std::pow(kp.q, kp.p);
   kp.cdiv = kp.s * qp;

@@ -88,10 +88,16 @@ def test_residual_f32_kernel(oracle, shape):
 # 8 x 8 x 8 CTAs of 32 x 32 x 16 cells: large enough for the register-blocked
 # FP32 residual kernel (which needs at least 2 x 152 such CTAs)
 RB_SHAPE = (128, 256, 256)
+# The register-blocked kernels run one wave of CTAs, each marching an equal
+# share of the (32 x 32 column, z-plane) pairs in one or two z-segments.  On
+# a 152-SM GB300 some shares of this grid end in one-plane segments for both
+# the residual (304 CTAs) and the line search (456 CTAs).
+RB_SHAPE_SHORT = (32, 512, 512)
 
 
+@pytest.mark.parametrize("shape", [RB_SHAPE, RB_SHAPE_SHORT])
 @pytest.mark.parametrize("p", [4.0, 3.0])
-def test_residual_f32_register_blocked(oracle, p):
+def test_residual_f32_register_blocked(oracle, p, shape):
     """The register-blocked FP32 residual kernel against the FP64 oracle on
     a grid that selects it.  Rough fields (as in the FP64 parity test): a
     misplaced neighbour or vertex then changes the result by O(1) relative,
@@ -99,22 +105,22 @@ def test_residual_f32_register_blocked(oracle, p):
     pass pair, against terms of size ~144 |u| s eps^2 / h^4) stays within
     ~1e-5 relative.  (With smooth fields at h = 2 pi / 256 the same rounding
     is ~1e-3 of the much smaller residual.)"""
-    P, h = _problem(oracle, 4, RB_SHAPE, p)
-    u = (rng.standard_normal(RB_SHAPE) * 0.3).astype(np.float32)
-    f = rng.standard_normal(RB_SHAPE).astype(np.float32)
-    S = Solver(4, RB_SHAPE, h, p, P.s, P.eps)
-    r = torch.empty(RB_SHAPE, dtype=torch.float32, device="cuda")
+    P, h = _problem(oracle, 4, shape, p)
+    u = (rng.standard_normal(shape) * 0.3).astype(np.float32)
+    f = rng.standard_normal(shape).astype(np.float32)
+    S = Solver(4, shape, h, p, P.s, P.eps)
+    r = torch.empty(shape, dtype=torch.float32, device="cuda")
     S.residual_f32(torch.from_numpy(u).cuda(), torch.from_numpy(f).cuda(), r)
     ref = oracle.residual4(u.astype(np.float64), f.astype(np.float64), P)
     assert rel(host(r).astype(np.float64), ref) <= 1e-4
 
 
+@pytest.mark.parametrize("shape", [RB_SHAPE, RB_SHAPE_SHORT])
 @pytest.mark.parametrize("p", [4.0, 3.0])
-def test_mixed_solve_register_blocked(p):
+def test_mixed_solve_register_blocked(p, shape):
     """Mixed precision on a grid that selects the register-blocked FP32
     residual and line-search kernels (inner correction form, p = 4 and a
     general p): the solution agrees with the plain FP64 solve to 1e-9."""
-    shape = RB_SHAPE
     h = 2 * np.pi / shape[-1]
     f = smooth_random(shape, K=8, seed=31)
     out = {}
