@@ -173,6 +173,19 @@ psd_status psd_set_history(psd_handle h, double* alpha_hist, double* res_hist,
 psd_status psd_residual_f32(psd_handle h, const float* u, const float* f,
                             float* r);
 
+/* FP64 residual by the kernel variant of the mixed solve's outer residual,
+ * for tests: r = f - N_h[u] (order 6: the local part, without T_h) with the
+ * linear part (z-pair sums, vertex gradients, both Laplacian passes of
+ * Sec. 5.1) in exact 64-bit fixed point, q = round(u 2^S), and the p = 4
+ * flux part in float-float; only the final combination is FP64.  S = 55 - e
+ * for max|u| (1 + 2^-20) < 2^e, returned in *scale.  Applies to p = 4 on 3D
+ * grids with nx >= 32 and ny >= 8, and max|u| in [2^-65, 2^40); otherwise
+ * *scale = 0 and r is not written.  u, f, r: device, N doubles; scale: host.
+ * The solver's bound on the float-float error of the flux part is not
+ * checked here.  Errors: PSD_ERR_INVALID for null pointers.                */
+psd_status psd_residual_fixed(psd_handle h, const double* u, const double* f,
+                              double* r, int* scale);
+
 /* Kernel classes reported by psd_profile_read (index = class).            */
 enum {
   PSD_PROF_RESIDUAL_FP64 = 0, PSD_PROF_RESIDUAL_FP32 = 1,

@@ -88,6 +88,7 @@ def load_library(build_if_missing=True):
     lib.psd_solve.argtypes = [H, D, D, D, D, ctypes.POINTER(PSDInfo)]
     lib.psd_set_history.argtypes = [H, P, P, ctypes.c_int]
     lib.psd_residual_f32.argtypes = [H, F, F, F]
+    lib.psd_residual_fixed.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_int)]
     lib.psd_precond_solve_f32.argtypes = [H, F, F]
     lib.psd_energy.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.psd_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
@@ -111,7 +112,7 @@ def load_library(build_if_missing=True):
     lib.psd_status_string.argtypes = [ctypes.c_int]
     lib.psd_status_string.restype = ctypes.c_char_p
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
-                 "psd_set_history", "psd_residual_f32", "psd_last_error", "psd_profile",
+                 "psd_set_history", "psd_residual_f32", "psd_residual_fixed", "psd_last_error", "psd_profile",
                  "psd_profile_read", "psd_profile_classes", "psd_residual_noalloc", "psd_noalloc_last_error",
                  "psd_precond_solve_f32", "psd_energy",
                  "psd_hvp",
@@ -231,6 +232,14 @@ def psd_residual_f32(handle, u, f, r):
                                            _ptr(r, "float32")), handle)
 
 
+def psd_residual_fixed(handle, u, f, r):
+    """FP64 residual by the fixed-point / float-float kernel variant; returns
+    the fixed-point scale S (0: the variant does not apply, r untouched)."""
+    scale = ctypes.c_int()
+    _check(load_library().psd_residual_fixed(handle, _ptr(u), _ptr(f), _ptr(r), ctypes.byref(scale)), handle)
+    return scale.value
+
+
 def psd_residual_noalloc(shape, h, p, s, eps, u, f, r, stream=None):
     """Fourth-order residual and norms without a handle or any device
     allocation (see include/psd.h).  Returns (||r||_2, max|r|)."""
@@ -333,6 +342,9 @@ class Solver:
 
     def residual_f32(self, u, f, r):
         psd_residual_f32(self.handle, u, f, r)
+
+    def residual_fixed(self, u, f, r):
+        return psd_residual_fixed(self.handle, u, f, r)
 
     def precond_solve_f32(self, r, d):
         psd_precond_solve_f32(self.handle, r, d)

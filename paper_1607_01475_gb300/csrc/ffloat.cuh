@@ -254,6 +254,27 @@ __host__ __device__ __forceinline__ double ff_to_double_bits(ff x) {
   return ff_bitsd(sgn | ((unsigned long long)(e + 1023) << 52) | ((unsigned long long)n & 0xFFFFFFFFFFFFFULL));
 }
 
+// ---- fixed point: v -> round(v 2^S) as a 64-bit integer (ties away from
+// zero) by bit manipulation, for |v| 2^S < 2^62 (the caller picks S from a
+// bound on |v|; larger values are not representable).  Sums and differences
+// of such integers are exact, which the FP64 residual uses for its linear
+// part.  Subnormal v is handled; NaN and infinity are not (the caller
+// excludes them).
+__host__ __device__ __forceinline__ long long fx_from_double(double v, int S) {
+  const unsigned long long b = ff_dbits(v);
+  const int E = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFULL) | (E ? (1ULL << 52) : 0ULL);
+  const int sh = (E ? E : 1) - 1075 + S;  // |v| = m 2^(E - 1075), subnormal: E = 1 without the implicit bit
+  unsigned long long a = 0;
+  if (sh >= 0)
+    a = m << (sh < 10 ? sh : 9);  // sh <= 9 when |v| 2^S < 2^62
+  else if (sh > -54)
+    a = (m + (1ULL << (-sh - 1))) >> (-sh);
+  return (b >> 63) ? -(long long)a : (long long)a;
+}
+// 2^-S as a double (|S| <= 1000), by bits
+__host__ __device__ __forceinline__ double fx_unit(int S) { return ff_bitsd((unsigned long long)(1023 - S) << 52); }
+
 // Arithmetic operators so that the line-FFT templates run on ff (sums with
 // the butterfly-grade ff_add_fast).
 __host__ __device__ __forceinline__ ff operator+(ff a, ff b) { return ff_add_fast(a, b); }

@@ -13,6 +13,7 @@
 // (2 vertex planes) in shared memory.  Every vertex flux and every Laplacian
 // value is computed once per CTA.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <type_traits>
 
@@ -626,15 +627,17 @@ __global__ void __launch_bounds__(NT)
 }
 
 // max |G|^2 over the vertices of an FP32 field (one vertex per thread,
-// grid-stride over the vertex planes; G from the 8 surrounding cells).
+// grid-stride over the vertex planes; G from the 8 surrounding cells) into
+// ctrl->res_linf, and max |u| into ctrl->res_l2 (+inf if a value is not
+// finite).
 __global__ void __launch_bounds__(NT) k_gradmax(const float* __restrict__ u, KParams kp, Ctrl* ctrl,
                                                 double* partials) {
-  __shared__ float sred[32];
+  __shared__ float sred[32 * 2];
   __shared__ int sflag;
   const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
   const int lx = __ffs(nx) - 1, lxy = lx + __ffs(ny) - 1;  // sizes are powers of two
   const size_t plane = (size_t)nx * ny, n = plane * nz;
-  float m = 0.0f;
+  float m = 0.0f, um = 0.0f;
   for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
     const int x = (int)(i & (nx - 1)), y = (int)((i >> lx) & (ny - 1)), z = (int)(i >> lxy);
     const int x1 = (x + 1) & (nx - 1), y1 = (y + 1) & (ny - 1), z1 = (z + 1) & (nz - 1);
@@ -647,14 +650,17 @@ __global__ void __launch_bounds__(NT) k_gradmax(const float* __restrict__ u, KPa
     const float g1 = ((u010 - u000) + (u011 - u001)) + ((u110 - u100) + (u111 - u101));
     const float g2 = ((u100 - u000) + (u101 - u001)) + ((u110 - u010) + (u111 - u011));
     m = fmaxf(m, g0 * g0 + g1 * g1 + g2 * g2);
+    const float au = fabsf(u000);
+    um = (au <= FLT_MAX) ? fmaxf(um, au) : INFINITY;  // NaN or infinity: +inf
   }
-  float v[1] = {m};
-  block_reduce<float, 1, true>(v, sred);
-  if (publish_and_check_last<float>(v, 1, reinterpret_cast<float*>(partials), &ctrl->counter[CS_MID], &sflag)) {
-    float tt[1];
-    gather_partials<float, 1, true>(tt, reinterpret_cast<const float*>(partials), sred);
+  float v[2] = {m, um};
+  block_reduce<float, 2, true, true>(v, sred);
+  if (publish_and_check_last<float>(v, 2, reinterpret_cast<float*>(partials), &ctrl->counter[CS_MID], &sflag)) {
+    float tt[2];
+    gather_partials<float, 2, true, true>(tt, reinterpret_cast<const float*>(partials), sred);
     if (threadIdx.x == 0) {
       ctrl->res_linf = (double)tt[0];
+      ctrl->res_l2 = (double)tt[1];
       ctrl->counter[CS_MID] = 0;
     }
   }
@@ -800,68 +806,68 @@ int pick_zc(int nz, int nblk_xy) {
   return zc;
 }
 
-// Launch geometry of the residual kernels.  3D FP32 grids large enough to
-// fill the GPU with 32 x 32 tiles take the register-blocked kernel (the FP32
-// residual is bound by shared-memory traffic); FP64 keeps the column kernel
-// (bound by its FP64 operations); small tiles take the general kernel.
+// Launch geometry of the residual and line-search kernels (ctas_per_sm =
+// the residency their __launch_bounds__ guarantee).  3D FP32 grids large
+// enough to fill the GPU with 32 x 32 tiles take the register-blocked
+// kernels (the FP32 residual is bound by instruction issue and shared-memory
+// traffic); FP64 and smaller grids the column kernels; tiles below 32 x 8
+// the general kernel.  The register-blocked and column kernels run one wave
+// of CTAs: the CTAs per SM times the SMs (cached in KParams at setup, so
+// captured and direct launches agree and the partial sums come in the same
+// order), at most one CTA per 16 (8) column-planes.
 enum ResKind { RK_2D, RK_SMALL3D, RK_COL, RK_RB4 };
 struct ResGeom {
   int kind;
   dim3 grid;
   int zc;
 };
-ResGeom res_geometry(const KParams& kp, bool fp32) {
+ResGeom res_geometry(const KParams& kp, bool fp32, int ctas_per_sm) {
   ResGeom g{RK_2D, dim3(1, 1, 1), 1};
   if (kp.dim != 3) {
     const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY2 ? kp.ny : BY2;
     g.grid = dim3(kp.nx / TX, kp.ny / TY);
     return g;
   }
+  const long long wave = (long long)ctas_per_sm * kp.nsm;
   if (fp32 && kp.nx % 32 == 0 && kp.ny % 32 == 0 && kp.nz >= 16 &&
       (long long)(kp.nx / 32) * (kp.ny / 32) * (kp.nz / 16) >= 2 * 152 &&
       (long long)(kp.nx / 32) * (kp.ny / 32) * kp.nz < (1LL << 31)) {
-    // one wave of CTAs sized at launch (rb_wave); grid holds the number of
-    // column-planes, the most CTAs a launch can use
+    const long long w = (long long)(kp.nx / 32) * (kp.ny / 32) * kp.nz;
     g.kind = RK_RB4;
-    g.grid = dim3((unsigned)((kp.nx / 32) * (kp.ny / 32) * kp.nz));
+    g.grid = dim3((unsigned)std::min(wave, w / 16));
     g.zc = 0;
     return g;
   }
   const int TX = kp.nx < BX ? kp.nx : BX, TY = kp.ny < BY3 ? kp.ny : BY3;
   const int gx = kp.nx / TX, gy = kp.ny / TY;
+  const long long w = (long long)gx * gy * kp.nz;
+  if (kp.nx >= 32 && kp.ny >= 8 && w < (1LL << 31)) {
+    g.kind = RK_COL;
+    g.grid = dim3((unsigned)std::max(1LL, std::min(wave, w / 8)));
+    g.zc = 0;
+    return g;
+  }
   g.zc = pick_zc(kp.nz, gx * gy);
   g.grid = dim3(gx, gy, kp.nz / g.zc);
-  g.kind = (kp.nx >= 32 && kp.ny >= 8) ? RK_COL : RK_SMALL3D;
+  g.kind = RK_SMALL3D;
   return g;
-}
-
-// CTAs of one full wave of a register-blocked kernel: the CTAs per SM that
-// its __launch_bounds__ guarantee (registers; the static shared memory of
-// that many CTAs fits an SM) times the SMs, at most `limit` (the column-planes).
-// Fixed per device, so the partial sums, and the results, do not depend on
-// whether a launch is captured into a graph.
-inline unsigned rb_wave(const KParams& kp, int ctas_per_sm, unsigned limit) {
-  return std::min<unsigned>((unsigned)(ctas_per_sm * kp.nsm), limit);
 }
 
 template <typename T, int PK, int MODE>
 cudaError_t res_impl(const ResArgs<T>& a, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st) {
-  const ResGeom g = res_geometry(kp, sizeof(T) == 4);
+  const ResGeom g = res_geometry(kp, sizeof(T) == 4, 2);  // __launch_bounds__(256, 2)
   switch (g.kind) {
     case RK_RB4:
-      if constexpr (sizeof(T) == 4) {
-        const unsigned nb = rb_wave(kp, 2, g.grid.x);  // __launch_bounds__(256, 2)
-        k_res3d_rb<T, PK, MODE, 4><<<nb, NT, 0, st>>>(a, kp, ctrl, partials);
-      }
+      if constexpr (sizeof(T) == 4) k_res3d_rb<T, PK, MODE, 4><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials);
       break;
     case RK_COL:
       if constexpr (sizeof(T) == 8 && MODE == RM_PLAIN && PK == PK_4) {
-        if (a.fluxff) {
-          k_res3d_col<T, PK, MODE, true><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
+        if (a.fluxff && a.d == nullptr && a.fxs >= 15 && a.fxs <= 120) {
+          k_res3d_col<T, PK, MODE, true><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials);
           break;
         }
       }
-      k_res3d_col<T, PK, MODE><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
+      k_res3d_col<T, PK, MODE><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials);
       break;
     case RK_SMALL3D:
       k_res3d<T, PK, MODE><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials, g.zc);
@@ -875,16 +881,14 @@ cudaError_t res_impl(const ResArgs<T>& a, const KParams& kp, Ctrl* ctrl, double*
 template <typename T, int PK, bool INNER>
 cudaError_t ls_impl(const T* u, const T* ubase, const T* d, const KParams& kp, Ctrl* ctrl, double* partials,
                     cudaStream_t st) {
-  const ResGeom g = res_geometry(kp, sizeof(T) == 4);  // the same tiles as the residual
+  // the same tiles as the residual; __launch_bounds__(256, 3)
+  const ResGeom g = res_geometry(kp, sizeof(T) == 4, 3);
   switch (g.kind) {
     case RK_RB4:
-      if constexpr (sizeof(T) == 4) {
-        const unsigned nb = rb_wave(kp, 3, g.grid.x);  // __launch_bounds__(256, 3)
-        k_ls3d_rb<T, PK, INNER, 4><<<nb, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials);
-      }
+      if constexpr (sizeof(T) == 4) k_ls3d_rb<T, PK, INNER, 4><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials);
       break;
     case RK_COL:
-      k_ls3d_col<T, PK, INNER><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, g.zc);
+      k_ls3d_col<T, PK, INNER><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials);
       break;
     case RK_SMALL3D:
       k_ls3d<T, PK, INNER><<<g.grid, NT, 0, st>>>(u, ubase, d, kp, ctrl, partials, g.zc);
@@ -913,7 +917,7 @@ cudaError_t launch_residual(const ResArgs<T>& a, int mode, int pk, const KParams
 }
 
 long long residual_grid_blocks(const KParams& kp, bool fp32) {
-  const ResGeom g = res_geometry(kp, fp32);
+  const ResGeom g = res_geometry(kp, fp32, 2);
   return (long long)g.grid.x * g.grid.y * g.grid.z;
 }
 

@@ -84,7 +84,9 @@ struct ResArgs {
   T* r;            // residual (order 6: local part, without T_h)
   int norm;        // 1: reduce ||r|| into ctrl and decide convergence
   int update_iter; // 1: this call advances the iteration count
-  int fluxff;      // FP64 plain, p = 4, 3D: flux part in float-float (see k_res3d_col)
+  int fluxff;      // FP64 plain without d, p = 4, 3D: fixed-point linear part and
+                   // float-float flux (see k_res3d_col)
+  int fxs;         // with fluxff: the fixed-point scale S (u = q 2^-S), in [15, 120]
 };
 
 // r = f - N_h^{loc}[u_in + alpha d] (plain) or

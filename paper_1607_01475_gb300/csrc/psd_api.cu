@@ -444,14 +444,16 @@ psd_status ensure_fp32(psd_context* c) {
 }
 
 // Whether the FP64 residual of the current iterate (its FP32 copy in u32)
-// may evaluate the flux part in float-float: p = 4, 3D column kernel, and
-// a worst-case error bound of that part,
+// may take the fixed-point linear part and the float-float flux part: p = 4,
+// 3D column kernel, and a worst-case error bound of the flux part,
 //   |Omega|^{1/2} * 24 * 2^-47 * s q^4 * (2 max|G|)^3
 // (24 flux values per cell in the divergence, 2^-47 the double-word
 // precision, a factor 2 of margin on the FP32 estimate of max|G|), below
-// tol / 20.
-psd_status use_fluxff(psd_context* c, bool* out) {
-  *out = false;
+// tol / 20.  *fxs receives the fixed-point scale S (0: plain FP64): with
+// max|u| < 2^e (max|u32| (1 + 2^-20) bounds it, as u32 = fl32(u)),
+// S = 55 - e keeps |q| = |u| 2^S below 2^55; S must lie in [15, 120].
+psd_status use_fluxff(psd_context* c, int* fxs) {
+  *fxs = 0;
   const KParams& kp = c->kp;
   if (c->pk != psd::PK_4 || kp.dim != 3 || kp.nx < 32 || kp.ny < 8 || !(c->prm.tol > 0)) return PSD_OK;
   Ctrl h;
@@ -462,19 +464,24 @@ psd_status use_fluxff(psd_context* c, bool* out) {
   TRY(read_ctrl(c, c->ctrl2, h2));
   const double gmax = 2.0 * std::sqrt(std::max(h2.res_linf, 0.0));
   const double bound = std::sqrt((double)c->N * kp.hd) * 24.0 * std::ldexp(1.0, -47) * kp.cdiv * gmax * gmax * gmax;
-  *out = std::isfinite(bound) && bound < 0.05 * c->prm.tol;
+  const double umax = h2.res_l2;
+  if (!(std::isfinite(bound) && bound < 0.05 * c->prm.tol) || !std::isfinite(umax)) return PSD_OK;
+  int e = 0;
+  if (umax > 0.0) std::frexp(umax * (1.0 + std::ldexp(1.0, -20)), &e);  // umax (1 + 2^-20) < 2^e
+  const int S = 55 - e;
+  if (S >= 15 && S <= 120) *fxs = S;
   return PSD_OK;
 }
 
 // FP64 residual r = f - N_h[u] into r (order 6: P0[...] including T_h[u - g]),
 // norms into ctrl2 (res_l2, res_linf).  Uses W, Z as scratch (order 6).
 psd_status residual64(psd_context* c, const double* u, const double* f, const double* g, double* r,
-                      bool fluxff = false) {
+                      int fxs = 0) {
   const KParams& kp = c->kp;
   Ctrl h;
   init_ctrl(h, -1.0, 1 << 30);
   TRY(upload_ctrl(c, c->ctrl2, h));
-  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, r, kp.order == 4 ? 1 : 0, 0, fluxff ? 1 : 0};
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, r, kp.order == 4 ? 1 : 0, 0, fxs ? 1 : 0, fxs};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
   if (kp.order == 6) {
     // r <- P0[r_loc - T_h[u - g]] through the spectrum
@@ -492,12 +499,12 @@ psd_status residual64(psd_context* c, const double* u, const double* f, const do
 // R32 <- (float) DHT(P0[f - N_h^{loc}[u]] - T_h[u - g]) = DHT(r_loc) - theta
 // with theta = DHT(T_h[u - g]) in Z (the subtraction, the rounding and the
 // Parseval norm fused into the last transform pass); ||R||_2 into *res.
-psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f, double* res, bool fluxff) {
+psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f, double* res, int fxs) {
   const KParams& kp = c->kp;
   Ctrl h;
   init_ctrl(h, -1.0, 1 << 30);
   TRY(upload_ctrl(c, c->ctrl2, h));
-  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0, fluxff ? 1 : 0};
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0, fxs ? 1 : 0, fxs};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
   const int nrows = kp.ny * kp.nz;
   psd::ff* x = reinterpret_cast<psd::ff*>(c->W);  // transformed in place, float-float pairs after the x pass
@@ -628,15 +635,15 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
       if (six) TRY(dht_theta_ff(c, nullptr, delta, dsum));
       { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, delta, c->u32, c->N, dsum, c->st)); }
     }
-    bool fluxff = false;
-    TRY(use_fluxff(c, &fluxff));
+    int fxs = 0;
+    TRY(use_fluxff(c, &fxs));
     if (six) {
       // the outer residual stays in the transform domain; the inner solve adds
       // it to its own transformed residual in the middle pass
-      TRY(outer_residual6_spec(c, u, f, &res, fluxff));
+      TRY(outer_residual6_spec(c, u, f, &res, fxs));
       resinf = -1.0;
     } else {
-      TRY(residual64(c, u, f, g, c->W, fluxff));
+      TRY(residual64(c, u, f, g, c->W, fxs));
       Ctrl h2;
       TRY(read_ctrl(c, c->ctrl2, h2));
       res = h2.res_l2;
@@ -967,6 +974,32 @@ psd_status psd_residual_f32(psd_handle c, const float* u, const float* f, float*
   ResArgs<float> a{u, nullptr, nullptr, f, nullptr, r, 0, 0};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_PLAIN, c->pk, c->kp, c->ctrl2, c->partials, c->st)); }
   CK(cudaStreamSynchronize(c->st));
+  return PSD_OK;
+}
+
+psd_status psd_residual_fixed(psd_handle c, const double* u, const double* f, double* r, int* scale) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u || !f || !r || !scale) return fail(c, PSD_ERR_INVALID, "u, f, r and scale are required");
+  *scale = 0;
+  const KParams& kp = c->kp;
+  if (c->pk != psd::PK_4 || kp.dim != 3 || kp.nx < 32 || kp.ny < 8) return PSD_OK;
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+  Ctrl h2;
+  TRY(read_ctrl(c, c->ctrl2, h2));
+  const double umax = h2.res_linf;
+  if (!std::isfinite(umax)) return PSD_OK;
+  int e = 0;
+  if (umax > 0.0) std::frexp(umax * (1.0 + std::ldexp(1.0, -20)), &e);
+  const int S = 55 - e;
+  if (S < 15 || S > 120) return PSD_OK;
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, r, 0, 0, 1, S};
+  { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
+  CK(cudaStreamSynchronize(c->st));
+  *scale = S;
   return PSD_OK;
 }
 

@@ -145,11 +145,12 @@ __device__ __forceinline__ T warp_max(T v) {
 
 // Reduce M values of type A over the block (fixed order: warp butterflies,
 // then warp 0 over the warp results); the result is valid in thread 0.  The
-// last value is reduced with max when LASTMAX is set.  FP32 kernels reduce
+// last value is reduced with max when LASTMAX is set, every value when
+// ALLMAX is.  FP32 kernels reduce
 // in float (GB300 issues FP64 at 1/64 of the FP32 rate), FP64 kernels in
 // double.  Requires blockDim to be a multiple of 32 (<= 1024) or smaller
 // than 32 (then thread 0 sums serially); uses a shared scratch of 32*M A's.
-template <typename A, int M, bool LASTMAX>
+template <typename A, int M, bool LASTMAX, bool ALLMAX = false>
 __device__ __forceinline__ void block_reduce(A (&v)[M], A* sh) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
@@ -162,7 +163,7 @@ __device__ __forceinline__ void block_reduce(A (&v)[M], A* sh) {
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         A acc = sh[m];
-        for (int t = 1; t < nthr; ++t) acc = (LASTMAX && m == M - 1) ? fmax(acc, sh[t * M + m]) : acc + sh[t * M + m];
+        for (int t = 1; t < nthr; ++t) acc = (ALLMAX || (LASTMAX && m == M - 1)) ? fmax(acc, sh[t * M + m]) : acc + sh[t * M + m];
         v[m] = acc;
       }
     }
@@ -171,7 +172,7 @@ __device__ __forceinline__ void block_reduce(A (&v)[M], A* sh) {
   }
   const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
 #pragma unroll
-  for (int m = 0; m < M; ++m) v[m] = (LASTMAX && m == M - 1) ? warp_max(v[m]) : warp_sum(v[m]);
+  for (int m = 0; m < M; ++m) v[m] = (ALLMAX || (LASTMAX && m == M - 1)) ? warp_max(v[m]) : warp_sum(v[m]);
   __syncthreads();
   if (lane == 0) {
 #pragma unroll
@@ -181,8 +182,8 @@ __device__ __forceinline__ void block_reduce(A (&v)[M], A* sh) {
   if (wid == 0) {
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      A x = (lane < nw) ? sh[lane * M + m] : ((LASTMAX && m == M - 1) ? A(-1) : A(0));
-      v[m] = (LASTMAX && m == M - 1) ? warp_max(x) : warp_sum(x);
+      A x = (lane < nw) ? sh[lane * M + m] : ((ALLMAX || (LASTMAX && m == M - 1)) ? A(-1) : A(0));
+      v[m] = (ALLMAX || (LASTMAX && m == M - 1)) ? warp_max(x) : warp_sum(x);
     }
   }
   __syncthreads();
@@ -209,21 +210,21 @@ __device__ __forceinline__ bool publish_and_check_last(const A* v, int M, A* par
 
 // In the last block: sum the partials of all blocks in a fixed order (each
 // thread a strided subset, then the block tree), result in thread 0.
-template <typename A, int M, bool LASTMAX>
+template <typename A, int M, bool LASTMAX, bool ALLMAX = false>
 __device__ __forceinline__ void gather_partials(A (&out)[M], const A* partials, A* sh) {
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
   const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
 #pragma unroll
-  for (int m = 0; m < M; ++m) out[m] = (LASTMAX && m == M - 1) ? A(-1) : A(0);
+  for (int m = 0; m < M; ++m) out[m] = (ALLMAX || (LASTMAX && m == M - 1)) ? A(-1) : A(0);
   for (unsigned int b = tid; b < nb; b += nthr) {
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       A x = __ldcg(partials + (size_t)b * M + m);
-      out[m] = (LASTMAX && m == M - 1) ? fmax(out[m], x) : out[m] + x;
+      out[m] = (ALLMAX || (LASTMAX && m == M - 1)) ? fmax(out[m], x) : out[m] + x;
     }
   }
-  block_reduce<A, M, LASTMAX>(out, sh);
+  block_reduce<A, M, LASTMAX, ALLMAX>(out, sh);
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {  // n a power of two

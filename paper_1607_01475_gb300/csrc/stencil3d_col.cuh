@@ -34,17 +34,24 @@
 namespace psd {
 namespace {
 
-// FFX (FP64, plain mode, p = 4): the flux part -- |G|^2 G, its z-sums S and
-// the divergence -- is evaluated in float-float arithmetic from the FP64
-// vertex gradients, halving the FP64 operations per cell; the gradients,
-// both Laplacian passes and the residual stay FP64.  The caller selects it
-// only when the worst-case float-float error of that part is far below the
-// solve tolerance (it scales with s q^4 max|G|^3).
+// FFX (FP64, plain mode without an update, p = 4): no FP64 arithmetic
+// before the final combination.  The linear part runs in 64-bit fixed
+// point: each u enters as q = round(u 2^S) (a.fxs = S, picked by the caller
+// from a bound on |u| so that |q| <= 2^55), and the z-pair sums, vertex
+// gradients and both Laplacian passes are exact integer sums (|h^4 Delta_h^2
+// q| <= 144 2^55 < 2^63).  The flux part -- |G|^2 G, its z-sums S and the
+// divergence -- is evaluated in float-float from the exact gradients.  Only
+// r = (f - cu u) + (cdiv div - cbih bih) and the norms are FP64, so the
+// residual is that of u rounded to the grid 2^-S (at most 2^-56 max|u| away,
+// below the rounding of the FP64 Laplacian sums it replaces).  The caller
+// selects it only when the worst-case float-float error of the flux part is
+// far below the solve tolerance (it scales with s q^4 max|G|^3).
 template <typename T, int PK, int MODE, bool FFX = false>
 __global__ void __launch_bounds__(256, 2)
-    k_res3d_col(ResArgs<T> a, KParams kp, Ctrl* ctrl, double* partials, int zc) {
+    k_res3d_col(ResArgs<T> a, KParams kp, Ctrl* ctrl, double* partials) {
   static_assert(!FFX || (sizeof(T) == 8 && MODE == RM_PLAIN && PK == PK_4), "FFX: FP64 plain p = 4 only");
-  using FT = typename std::conditional<FFX, ff, T>::type;  // arithmetic type of the flux part
+  using FT = typename std::conditional<FFX, ff, T>::type;         // arithmetic type of the flux part
+  using LT = typename std::conditional<FFX, long long, T>::type;  // and of the linear part
   if (ctrl->done) return;
   constexpr int TX = 32, TY = 8;
   constexpr int UX = TX + 4, UY = TY + 4, UN = UX * UY;  // U tile, halo 2
@@ -55,10 +62,10 @@ __global__ void __launch_bounds__(256, 2)
   constexpr bool BASE = MODE != RM_PLAIN;  // a base field B enters the flux
   constexpr int NLH = 2 * LX + 2 * TY;                   // Laplacian halo cells (84)
   constexpr int NVH = VY + TX;                           // vertex halo (41)
-  __shared__ T sU[3][UY][UX];
-  __shared__ T sL[2][LY][LX];
-  __shared__ T sP[LY][LX];
-  __shared__ T sM[LY][LX];
+  __shared__ LT sU[3][UY][UX];
+  __shared__ LT sL[2][LY][LX];
+  __shared__ LT sP[LY][LX];
+  __shared__ LT sM[LY][LX];
   __shared__ T sPb[BASE ? LY : 1][BASE ? LX : 1];
   __shared__ T sMb[BASE ? LY : 1][BASE ? LX : 1];
   __shared__ T sS[3][VY][VX];
@@ -67,263 +74,298 @@ __global__ void __launch_bounds__(256, 2)
 
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
   const size_t plane = (size_t)nx * ny;
   const bool upd = a.d != nullptr;
   const T alpha = upd ? (T)ctrl->alpha : T(0);
   const KConst<T>& C = kconst<T>(kp);
   const T cdiv = C.cdiv, cbih = C.cbih, cu = C.cu;
   const T beta = C.beta;
+  // fixed point (FFX): u = q 2^-S; the gradients enter the flux scaled by
+  // 2^-S (a float, S in [15, 120]); cu and cbih absorb 2^-S
+  const int fxs = FFX ? a.fxs : 0;
+  const float gsc = FFX ? __int_as_float((127 - fxs) << 23) : 1.0f;
+  const T cuq = FFX ? cu * (T)fx_unit(fxs) : cu, cbihq = FFX ? cbih * (T)fx_unit(fxs) : cbih;
 
-  // this thread's U-tile elements (flattened e = tid, tid + 256) and where
-  // they land in the halo-1 P/M tile
-  int uoff[2], upm[2];
-  bool uval[2], uown[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int e = tid + 256 * k;
-    uval[k] = e < UN;
-    const int ly = e / UX, lx = e - ly * UX;
-    uoff[k] = ((y0 + ly - 2) & (ny - 1)) * nx + ((x0 + lx - 2) & (nx - 1));
-    uown[k] = uval[k] && lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2;
-    upm[k] = (uval[k] && ly >= 1 && ly <= LY && lx >= 1 && lx <= LX) ? (ly - 1) * LX + (lx - 1) : -1;
-  }
-  int boff[2];
-  bool bval[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int e = tid + 256 * k;
-    bval[k] = BASE && e < LN;
-    const int ly = e / LX, lx = e - ly * LX;
-    boff[k] = ((y0 + ly - 1) & (ny - 1)) * nx + ((x0 + lx - 1) & (nx - 1));
-  }
-  const int gown = (y0 + ty) * nx + x0 + tx;
-
-  T pu[2] = {T(0), T(0)}, pd[2] = {T(0), T(0)}, pb[2] = {T(0), T(0)};
-  T h1[2] = {T(0), T(0)}, h0[2] = {T(0), T(0)};  // U history: h1 newest stored plane, h0 the one before
-  T bprev[2] = {T(0), T(0)};
-  auto fetchU = [&](int zz) {
-    const size_t gz = (size_t)(zz & (nz - 1)) * plane;
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (uval[k]) {
-        pu[k] = a.u_in[gz + uoff[k]];
-        if (upd) pd[k] = a.d[gz + uoff[k]];
-      }
-  };
-  // store the prefetched plane zz into ring slot `slot` and shift the
-  // register history (h0 <- h1 <- new)
-  auto storeU = [&](int zz, int slot) {
-    const size_t gz = (size_t)(zz & (nz - 1)) * plane;
-    const bool ownplane = zz >= z0 && zz < z0 + zc;
-    T* dst = &sU[slot][0][0];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (uval[k]) {
-        T v = pu[k];
-        if (upd) {
-          v = v + alpha * pd[k];
-          if (ownplane && uown[k]) a.u_out[gz + uoff[k]] = v;
-        }
-        dst[tid + 256 * k] = v;
-        h0[k] = h1[k];
-        h1[k] = v;
-      }
-  };
-  // P/M of the vertex plane between the two newest history planes
-  auto storePM = [&]() {
-    T* P = &sP[0][0];
-    T* M = &sM[0][0];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (upm[k] >= 0) {
-        P[upm[k]] = h0[k] + h1[k];
-        M[upm[k]] = h1[k] - h0[k];
-      }
-  };
-  auto fetchB = [&](int zz) {
-    if (!BASE) return;
-    const size_t gz = (size_t)(zz & (nz - 1)) * plane;
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (bval[k]) pb[k] = a.ubase[gz + boff[k]];
-  };
-  // base P/M between bprev and the prefetched plane (first: only record)
-  auto storeB = [&](bool first) {
-    if (!BASE) return;
-    T* P = &sPb[0][0];
-    T* M = &sMb[0][0];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (bval[k]) {
-        if (!first) {
-          P[tid + 256 * k] = bprev[k] + pb[k];
-          M[tid + 256 * k] = pb[k] - bprev[k];
-        }
-        bprev[k] = pb[k];
-      }
-  };
-  // h^2 Delta_h U at halo-1 cell (ly, lx) of the plane in slot s0
-  auto lap_at = [&](int ly, int lx, int sm, int s0, int sp) -> T {
-    const T c = sU[s0][ly + 1][lx + 1];
-    const T sum = (sU[s0][ly + 1][lx] + sU[s0][ly + 1][lx + 2]) + (sU[s0][ly][lx + 1] + sU[s0][ly + 2][lx + 1]) +
-                  (sU[sm][ly + 1][lx + 1] + sU[sp][ly + 1][lx + 1]);
-    return sum - T(6) * c;
-  };
-  auto halo_lap_cell = [&](int h, int& ly, int& lx) {
-    if (h < LX) {
-      ly = 0;
-      lx = h;
-    } else if (h < 2 * LX) {
-      ly = LY - 1;
-      lx = h - LX;
-    } else if (h < 2 * LX + TY) {
-      ly = 1 + h - 2 * LX;
-      lx = 0;
-    } else {
-      ly = 1 + h - 2 * LX - TY;
-      lx = LX - 1;
-    }
-  };
-  auto lap_plane = [&](int sm, int s0, int sp, int ls) -> T {
-    const T own = lap_at(ty + 1, tx + 1, sm, s0, sp);
-    sL[ls][ty + 1][tx + 1] = own;
-    const int h = tid - (256 - NLH);
-    if (h >= 0) {
-      int ly, lx;
-      halo_lap_cell(h, ly, lx);
-      sL[ls][ly][lx] = lap_at(ly, lx, sm, s0, sp);
-    }
-    return own;
-  };
-  // Phi at vertex (vy, vx) of the current vertex plane (from sP/sM)
-  auto vphi = [&](int vy, int vx, FT (&F)[3]) {
-    T G[3];
-    G[0] = (sP[vy][vx + 1] - sP[vy][vx]) + (sP[vy + 1][vx + 1] - sP[vy + 1][vx]);
-    G[1] = (sP[vy + 1][vx] - sP[vy][vx]) + (sP[vy + 1][vx + 1] - sP[vy][vx + 1]);
-    G[2] = (sM[vy][vx] + sM[vy][vx + 1]) + (sM[vy + 1][vx] + sM[vy + 1][vx + 1]);
-    if constexpr (FFX) {
-      const ff g0 = ff_from_double_bits(G[0]), g1 = ff_from_double_bits(G[1]), g2 = ff_from_double_bits(G[2]);
-      const ff q2 = ff_add_fast(ff_add_fast(g0 * g0, g1 * g1), g2 * g2);
-      F[0] = q2 * g0;
-      F[1] = q2 * g1;
-      F[2] = q2 * g2;
-    } else if (BASE) {
-      T A[3];
-      A[0] = (sPb[vy][vx + 1] - sPb[vy][vx]) + (sPb[vy + 1][vx + 1] - sPb[vy + 1][vx]);
-      A[1] = (sPb[vy + 1][vx] - sPb[vy][vx]) + (sPb[vy + 1][vx + 1] - sPb[vy][vx + 1]);
-      A[2] = (sMb[vy][vx] + sMb[vy][vx + 1]) + (sMb[vy + 1][vx] + sMb[vy + 1][vx + 1]);
-      if (INNER)
-        flux_diff<PK>(A, G, beta, F);
-      else
-        flux_lin<PK>(A, G, beta, F);
-    } else {
-      flux<PK>(G, beta, F);
-    }
-  };
-  // the S sums in the arithmetic type of the flux (float-float pairs occupy
-  // the 8 bytes of an FP64 slot)
-  FT(*SS)[VY][VX] = reinterpret_cast<FT(*)[VY][VX]>(&sS[0][0][0]);
-  // own vertex (ty+1, tx+1) and, for tid < NVH, one halo vertex
-  const bool hv = tid < NVH;
-  const int hvy = tid < VY ? tid : 0;
-  const int hvx = tid < VY ? 0 : tid - VY + 1;
-  FT Fo[3] = {FT(0), FT(0), FT(0)}, Fh[3] = {FT(0), FT(0), FT(0)};  // Phi of the previous vertex plane
-  auto phi_plane = [&](bool first) {
-    FT F[3];
-    vphi(ty + 1, tx + 1, F);
-    if (!first) {
-      SS[0][ty + 1][tx + 1] = Fo[0] + F[0];
-      SS[1][ty + 1][tx + 1] = Fo[1] + F[1];
-      SS[2][ty + 1][tx + 1] = F[2] - Fo[2];
-    }
-    Fo[0] = F[0];
-    Fo[1] = F[1];
-    Fo[2] = F[2];
-    if (hv) {
-      vphi(hvy, hvx, F);
-      if (!first) {
-        SS[0][hvy][hvx] = Fh[0] + F[0];
-        SS[1][hvy][hvx] = Fh[1] + F[1];
-        SS[2][hvy][hvx] = F[2] - Fh[2];
-      }
-      Fh[0] = F[0];
-      Fh[1] = F[1];
-      Fh[2] = F[2];
-    }
-  };
-
-  // ---- prologue
-  // ring slots 0, 1, 2 hold U(z0-2), U(z0-1), U(z0); P/M of vertex plane z0-1/2
-  fetchU(z0 - 2);
-  storeU(z0 - 2, 0);
-  fetchU(z0 - 1);
-  storeU(z0 - 1, 1);
-  fetchU(z0);
-  storeU(z0, 2);
-  storePM();  // from (U(z0-1), U(z0))
-  fetchB(z0 - 1);
-  storeB(true);
-  fetchB(z0);
-  storeB(false);  // base P/M of plane z0 - 1/2
-  __syncthreads();
-  T Lm = lap_at(ty + 1, tx + 1, 0, 1, 2);  // lap'(z0 - 1), own column only
-  phi_plane(true);                         // Phi(z0 - 1/2) into registers
-  __syncthreads();
-  fetchU(z0 + 1);
-  storeU(z0 + 1, 0);  // history now (U(z0), U(z0+1))
-  __syncthreads();
-  int lz = 0;
-  T L0 = lap_plane(1, 2, 0, lz);  // lap'(z0)
-  __syncthreads();  // lap'(z0) read slot 1, which the first loop step overwrites
-  // loop convention: um = slot of U(z-1), u0 = U(z), u1 = U(z+1)
-  int um = 1, u0 = 2, u1 = 0;
-  fetchU(z0 + 2);
-  fetchB(z0 + 1);
-  T fr = a.f ? a.f[(size_t)(z0 & (nz - 1)) * plane + gown] : T(0);
-
+  // One wave of CTAs: the column-planes (w = column * nz + z, column = tile
+  // index, x fastest) are split into equal contiguous shares, each marched
+  // as one or more z-segments with their own prologue.
+  const int gx = nx / TX;
+  const int wtot = gx * (ny / TY) * nz;
+  const int wend = (int)((long long)wtot * (blockIdx.x + 1) / gridDim.x);
   T acc2 = T(0), accm = T(0);
-  for (int z = z0; z < z0 + zc; ++z) {
-    const int u2 = um;
-    storePM();        // vertex plane z + 1/2 from (U(z), U(z+1))
-    storeU(z + 2, u2);
-    storeB(false);    // base P/M of plane z + 1/2
-    __syncthreads();  // (A)
-    const T fcur = fr;
-    fetchU(z + 3);
-    fetchB(z + 2);
-    fr = a.f ? a.f[(size_t)((z + 1) & (nz - 1)) * plane + gown] : T(0);
-    const T Lp = lap_plane(u0, u1, u2, lz ^ 1);  // lap'(z+1)
-    phi_plane(false);                            // S/D for the cells of plane z
-    const T uc = sU[u0][ty + 2][tx + 2];
-    __syncthreads();  // (B)
-    const T bih = (((sL[lz][ty + 1][tx] + sL[lz][ty + 1][tx + 2]) + (sL[lz][ty][tx + 1] + sL[lz][ty + 2][tx + 1])) +
-                   (Lm + Lp)) -
-                  T(6) * L0;
-    const FT dx = (SS[0][ty][tx + 1] - SS[0][ty][tx]) + (SS[0][ty + 1][tx + 1] - SS[0][ty + 1][tx]);
-    const FT dy = (SS[1][ty + 1][tx] - SS[1][ty][tx]) + (SS[1][ty + 1][tx + 1] - SS[1][ty][tx + 1]);
-    const FT dz = (SS[2][ty][tx] + SS[2][ty][tx + 1]) + (SS[2][ty + 1][tx] + SS[2][ty + 1][tx + 1]);
-    T div;
-    if constexpr (FFX)
-      div = ff_to_double_bits((dx + dy) + dz);
-    else
-      div = (dx + dy) + dz;
-    T r;
-    if (INNER)
-      r = fcur - ((cu * uc + cbih * bih) - cdiv * div);
-    else if (HVP)
-      r = (cu * uc + cbih * bih) - cdiv * div;
-    else
-      r = (fcur - cu * uc) + (cdiv * div - cbih * bih);
-    a.r[(size_t)(z & (nz - 1)) * plane + gown] = r;
-    acc2 += HVP ? uc * r : r * r;
-    accm = fmax(accm, fabs(r));
-    Lm = L0;
-    L0 = Lp;
-    lz ^= 1;
-    um = u0;
-    u0 = u1;
-    u1 = u2;
+  for (int w = (int)((long long)wtot * blockIdx.x / gridDim.x); w < wend;) {
+    const int col = w / nz, z0 = w - col * nz;
+    const int zc = min(nz - z0, wend - w);
+    w += zc;
+    const int x0 = (col % gx) * TX, y0 = (col / gx) * TY;
+
+    // this thread's U-tile elements (flattened e = tid, tid + 256) and where
+    // they land in the halo-1 P/M tile
+    int uoff[2], upm[2];
+    bool uval[2], uown[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int e = tid + 256 * k;
+      uval[k] = e < UN;
+      const int ly = e / UX, lx = e - ly * UX;
+      uoff[k] = ((y0 + ly - 2) & (ny - 1)) * nx + ((x0 + lx - 2) & (nx - 1));
+      uown[k] = uval[k] && lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2;
+      upm[k] = (uval[k] && ly >= 1 && ly <= LY && lx >= 1 && lx <= LX) ? (ly - 1) * LX + (lx - 1) : -1;
+    }
+    int boff[2];
+    bool bval[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int e = tid + 256 * k;
+      bval[k] = BASE && e < LN;
+      const int ly = e / LX, lx = e - ly * LX;
+      boff[k] = ((y0 + ly - 1) & (ny - 1)) * nx + ((x0 + lx - 1) & (nx - 1));
+    }
+    const int gown = (y0 + ty) * nx + x0 + tx;
+
+    T pu[2] = {T(0), T(0)}, pd[2] = {T(0), T(0)}, pb[2] = {T(0), T(0)};
+    LT h1[2] = {LT(0), LT(0)}, h0[2] = {LT(0), LT(0)};  // U history: h1 newest stored plane, h0 the one before
+    T bprev[2] = {T(0), T(0)};
+    auto fetchU = [&](int zz) {
+      const size_t gz = (size_t)(zz & (nz - 1)) * plane;
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (uval[k]) {
+          pu[k] = a.u_in[gz + uoff[k]];
+          if (upd) pd[k] = a.d[gz + uoff[k]];
+        }
+    };
+    // store the prefetched plane zz into ring slot `slot` and shift the
+    // register history (h0 <- h1 <- new)
+    auto storeU = [&](int zz, int slot) {
+      const size_t gz = (size_t)(zz & (nz - 1)) * plane;
+      const bool ownplane = zz >= z0 && zz < z0 + zc;
+      LT* dst = &sU[slot][0][0];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (uval[k]) {
+          LT v;
+          if constexpr (FFX) {
+            v = fx_from_double(pu[k], fxs);
+          } else {
+            v = pu[k];
+            if (upd) {
+              v = v + alpha * pd[k];
+              if (ownplane && uown[k]) a.u_out[gz + uoff[k]] = v;
+            }
+          }
+          dst[tid + 256 * k] = v;
+          h0[k] = h1[k];
+          h1[k] = v;
+        }
+    };
+    // P/M of the vertex plane between the two newest history planes
+    auto storePM = [&]() {
+      LT* P = &sP[0][0];
+      LT* M = &sM[0][0];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (upm[k] >= 0) {
+          P[upm[k]] = h0[k] + h1[k];
+          M[upm[k]] = h1[k] - h0[k];
+        }
+    };
+    auto fetchB = [&](int zz) {
+      if (!BASE) return;
+      const size_t gz = (size_t)(zz & (nz - 1)) * plane;
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (bval[k]) pb[k] = a.ubase[gz + boff[k]];
+    };
+    // base P/M between bprev and the prefetched plane (first: only record)
+    auto storeB = [&](bool first) {
+      if (!BASE) return;
+      T* P = &sPb[0][0];
+      T* M = &sMb[0][0];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (bval[k]) {
+          if (!first) {
+            P[tid + 256 * k] = bprev[k] + pb[k];
+            M[tid + 256 * k] = pb[k] - bprev[k];
+          }
+          bprev[k] = pb[k];
+        }
+    };
+    // h^2 Delta_h U at halo-1 cell (ly, lx) of the plane in slot s0
+    auto lap_at = [&](int ly, int lx, int sm, int s0, int sp) -> LT {
+      const LT c = sU[s0][ly + 1][lx + 1];
+      const LT sum = (sU[s0][ly + 1][lx] + sU[s0][ly + 1][lx + 2]) + (sU[s0][ly][lx + 1] + sU[s0][ly + 2][lx + 1]) +
+                     (sU[sm][ly + 1][lx + 1] + sU[sp][ly + 1][lx + 1]);
+      return sum - LT(6) * c;
+    };
+    auto halo_lap_cell = [&](int h, int& ly, int& lx) {
+      if (h < LX) {
+        ly = 0;
+        lx = h;
+      } else if (h < 2 * LX) {
+        ly = LY - 1;
+        lx = h - LX;
+      } else if (h < 2 * LX + TY) {
+        ly = 1 + h - 2 * LX;
+        lx = 0;
+      } else {
+        ly = 1 + h - 2 * LX - TY;
+        lx = LX - 1;
+      }
+    };
+    auto lap_plane = [&](int sm, int s0, int sp, int ls) -> LT {
+      const LT own = lap_at(ty + 1, tx + 1, sm, s0, sp);
+      sL[ls][ty + 1][tx + 1] = own;
+      const int h = tid - (256 - NLH);
+      if (h >= 0) {
+        int ly, lx;
+        halo_lap_cell(h, ly, lx);
+        sL[ls][ly][lx] = lap_at(ly, lx, sm, s0, sp);
+      }
+      return own;
+    };
+    // Phi at vertex (vy, vx) of the current vertex plane (from sP/sM)
+    auto vphi = [&](int vy, int vx, FT (&F)[3]) {
+      LT G[3];
+      G[0] = (sP[vy][vx + 1] - sP[vy][vx]) + (sP[vy + 1][vx + 1] - sP[vy + 1][vx]);
+      G[1] = (sP[vy + 1][vx] - sP[vy][vx]) + (sP[vy + 1][vx + 1] - sP[vy][vx + 1]);
+      G[2] = (sM[vy][vx] + sM[vy][vx + 1]) + (sM[vy + 1][vx] + sM[vy + 1][vx + 1]);
+      if constexpr (FFX) {
+        // exact integer gradients -> float-float (within 2^-48), scaled by 2^-S
+        const ff g0 = ff_scale2(ff_from_double_bits(__ll2double_rn(G[0])), gsc);
+        const ff g1 = ff_scale2(ff_from_double_bits(__ll2double_rn(G[1])), gsc);
+        const ff g2 = ff_scale2(ff_from_double_bits(__ll2double_rn(G[2])), gsc);
+        const ff q2 = ff_add_fast(ff_add_fast(g0 * g0, g1 * g1), g2 * g2);
+        F[0] = q2 * g0;
+        F[1] = q2 * g1;
+        F[2] = q2 * g2;
+      } else if (BASE) {
+        T A[3];
+        A[0] = (sPb[vy][vx + 1] - sPb[vy][vx]) + (sPb[vy + 1][vx + 1] - sPb[vy + 1][vx]);
+        A[1] = (sPb[vy + 1][vx] - sPb[vy][vx]) + (sPb[vy + 1][vx + 1] - sPb[vy][vx + 1]);
+        A[2] = (sMb[vy][vx] + sMb[vy][vx + 1]) + (sMb[vy + 1][vx] + sMb[vy + 1][vx + 1]);
+        if (INNER)
+          flux_diff<PK>(A, G, beta, F);
+        else
+          flux_lin<PK>(A, G, beta, F);
+      } else {
+        flux<PK>(G, beta, F);
+      }
+    };
+    // the S sums in the arithmetic type of the flux (float-float pairs occupy
+    // the 8 bytes of an FP64 slot)
+    FT(*SS)[VY][VX] = reinterpret_cast<FT(*)[VY][VX]>(&sS[0][0][0]);
+    // own vertex (ty+1, tx+1) and, for tid < NVH, one halo vertex
+    const bool hv = tid < NVH;
+    const int hvy = tid < VY ? tid : 0;
+    const int hvx = tid < VY ? 0 : tid - VY + 1;
+    FT Fo[3] = {FT(0), FT(0), FT(0)}, Fh[3] = {FT(0), FT(0), FT(0)};  // Phi of the previous vertex plane
+    auto phi_plane = [&](bool first) {
+      FT F[3];
+      vphi(ty + 1, tx + 1, F);
+      if (!first) {
+        SS[0][ty + 1][tx + 1] = Fo[0] + F[0];
+        SS[1][ty + 1][tx + 1] = Fo[1] + F[1];
+        SS[2][ty + 1][tx + 1] = F[2] - Fo[2];
+      }
+      Fo[0] = F[0];
+      Fo[1] = F[1];
+      Fo[2] = F[2];
+      if (hv) {
+        vphi(hvy, hvx, F);
+        if (!first) {
+          SS[0][hvy][hvx] = Fh[0] + F[0];
+          SS[1][hvy][hvx] = Fh[1] + F[1];
+          SS[2][hvy][hvx] = F[2] - Fh[2];
+        }
+        Fh[0] = F[0];
+        Fh[1] = F[1];
+        Fh[2] = F[2];
+      }
+    };
+
+    // ---- prologue
+    // ring slots 0, 1, 2 hold U(z0-2), U(z0-1), U(z0); P/M of vertex plane z0-1/2
+    fetchU(z0 - 2);
+    storeU(z0 - 2, 0);
+    fetchU(z0 - 1);
+    storeU(z0 - 1, 1);
+    fetchU(z0);
+    storeU(z0, 2);
+    storePM();  // from (U(z0-1), U(z0))
+    fetchB(z0 - 1);
+    storeB(true);
+    fetchB(z0);
+    storeB(false);  // base P/M of plane z0 - 1/2
+    __syncthreads();
+    LT Lm = lap_at(ty + 1, tx + 1, 0, 1, 2);  // lap'(z0 - 1), own column only
+    phi_plane(true);                         // Phi(z0 - 1/2) into registers
+    __syncthreads();
+    fetchU(z0 + 1);
+    storeU(z0 + 1, 0);  // history now (U(z0), U(z0+1))
+    __syncthreads();
+    int lz = 0;
+    LT L0 = lap_plane(1, 2, 0, lz);  // lap'(z0)
+    __syncthreads();  // lap'(z0) read slot 1, which the first loop step overwrites
+    // loop convention: um = slot of U(z-1), u0 = U(z), u1 = U(z+1)
+    int um = 1, u0 = 2, u1 = 0;
+    fetchU(z0 + 2);
+    fetchB(z0 + 1);
+    T fr = a.f ? a.f[(size_t)(z0 & (nz - 1)) * plane + gown] : T(0);
+
+    for (int z = z0; z < z0 + zc; ++z) {
+      const int u2 = um;
+      storePM();        // vertex plane z + 1/2 from (U(z), U(z+1))
+      storeU(z + 2, u2);
+      storeB(false);    // base P/M of plane z + 1/2
+      __syncthreads();  // (A)
+      const T fcur = fr;
+      fetchU(z + 3);
+      fetchB(z + 2);
+      fr = a.f ? a.f[(size_t)((z + 1) & (nz - 1)) * plane + gown] : T(0);
+      const LT Lp = lap_plane(u0, u1, u2, lz ^ 1);  // lap'(z+1)
+      phi_plane(false);                             // S/D for the cells of plane z
+      const LT ucl = sU[u0][ty + 2][tx + 2];
+      __syncthreads();  // (B)
+      const LT bihl = (((sL[lz][ty + 1][tx] + sL[lz][ty + 1][tx + 2]) + (sL[lz][ty][tx + 1] + sL[lz][ty + 2][tx + 1])) +
+                       (Lm + Lp)) -
+                      LT(6) * L0;
+      // FFX: the integers in units of 2^-S (cuq, cbihq carry the factor)
+      T uc, bih;
+      if constexpr (FFX) {
+        uc = __ll2double_rn(ucl);
+        bih = __ll2double_rn(bihl);
+      } else {
+        uc = ucl;
+        bih = bihl;
+      }
+      const FT dx = (SS[0][ty][tx + 1] - SS[0][ty][tx]) + (SS[0][ty + 1][tx + 1] - SS[0][ty + 1][tx]);
+      const FT dy = (SS[1][ty + 1][tx] - SS[1][ty][tx]) + (SS[1][ty + 1][tx + 1] - SS[1][ty][tx + 1]);
+      const FT dz = (SS[2][ty][tx] + SS[2][ty][tx + 1]) + (SS[2][ty + 1][tx] + SS[2][ty + 1][tx + 1]);
+      T div;
+      if constexpr (FFX)
+        div = ff_to_double_bits((dx + dy) + dz);
+      else
+        div = (dx + dy) + dz;
+      T r;
+      if (INNER)
+        r = fcur - ((cu * uc + cbih * bih) - cdiv * div);
+      else if (HVP)
+        r = (cu * uc + cbih * bih) - cdiv * div;
+      else
+        r = (fcur - cuq * uc) + (cdiv * div - cbihq * bih);
+      a.r[(size_t)(z & (nz - 1)) * plane + gown] = r;
+      acc2 += HVP ? uc * r : r * r;
+      accm = fmax(accm, fabs(r));
+      Lm = L0;
+      L0 = Lp;
+      lz ^= 1;
+      um = u0;
+      u0 = u1;
+      u1 = u2;
+    }
+    __syncthreads();  // the next segment's prologue refills the shared tiles
   }
 
   T v[2] = {acc2, accm};
@@ -343,7 +385,7 @@ __global__ void __launch_bounds__(256, 2)
 template <typename T, int PK, bool INNER>
 __global__ void __launch_bounds__(256, 3)
     k_ls3d_col(const T* __restrict__ u, const T* __restrict__ ubase, const T* __restrict__ d, KParams kp,
-               Ctrl* ctrl, double* partials, int zc) {
+               Ctrl* ctrl, double* partials) {
   if (ctrl->done) return;
   if (PK != PK_4 && ctrl->c3 != 0.0) return;  // Newton already converged
   constexpr int TX = 32, TY = 8;
@@ -353,18 +395,23 @@ __global__ void __launch_bounds__(256, 3)
   __shared__ int sflag;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
   const size_t plane = (size_t)nx * ny;
   const T beta = kconst<T>(kp).beta, pm2 = kconst<T>(kp).pm2;
   const T trial = (PK == PK_4) ? T(0) : (T)ctrl->alpha;
-  int off[2];
+  // one wave of CTAs, each marching an equal share of the column-planes (as
+  // the residual column kernel)
+  const int gx = nx / TX;
+  const int wtot = gx * (ny / TY) * nz;
+  const int wend = (int)((long long)wtot * (blockIdx.x + 1) / gridDim.x);
+  int off[2], ely[2], elx[2];
   bool val[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int e = tid + 256 * k;
     val[k] = e < SN;
-    const int ly = e / SX, lx = e - ly * SX;
-    off[k] = ((y0 + ly) & (ny - 1)) * nx + ((x0 + lx) & (nx - 1));
+    ely[k] = e / SX;
+    elx[k] = e - ely[k] * SX;
+    off[k] = 0;
   }
   // prefetched plane: u, base and d kept apart until used a step later
   T pu[2] = {T(0), T(0)}, pbv[2] = {T(0), T(0)}, pdv[2] = {T(0), T(0)}, hu[2] = {T(0), T(0)},
@@ -402,18 +449,27 @@ __global__ void __launch_bounds__(256, 3)
     g[2] = (M[ty][tx] + M[ty][tx + 1]) + (M[ty + 1][tx] + M[ty + 1][tx + 1]);
   };
   T acc[3] = {T(0), T(0), T(0)};
-  fetch(z0);
-  store(0, true);
-  fetch(z0 + 1);
-  for (int z = z0; z < z0 + zc; ++z) {
-    const int buf = (z - z0) & 1;
-    store(buf, false);  // vertex plane z + 1/2
-    __syncthreads();
-    fetch(z + 2);
-    T av[3], bv[3];
-    grad(sPu[buf], sMu[buf], av);
-    grad(sPd[buf], sMd[buf], bv);
-    ls_accumulate<PK>(av, bv, trial, beta, pm2, acc);
+  for (int w = (int)((long long)wtot * blockIdx.x / gridDim.x); w < wend;) {
+    const int col = w / nz, z0 = w - col * nz;
+    const int zc = min(nz - z0, wend - w);
+    w += zc;
+    const int x0 = (col % gx) * TX, y0 = (col / gx) * TY;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) off[k] = ((y0 + ely[k]) & (ny - 1)) * nx + ((x0 + elx[k]) & (nx - 1));
+    fetch(z0);
+    store(0, true);
+    fetch(z0 + 1);
+    for (int z = z0; z < z0 + zc; ++z) {
+      const int buf = (z - z0) & 1;
+      store(buf, false);  // vertex plane z + 1/2
+      __syncthreads();
+      fetch(z + 2);
+      T av[3], bv[3];
+      grad(sPu[buf], sMu[buf], av);
+      grad(sPd[buf], sMd[buf], bv);
+      ls_accumulate<PK>(av, bv, trial, beta, pm2, acc);
+    }
+    __syncthreads();  // the next segment writes the shared buffers again
   }
   T v[3] = {acc[0], acc[1], acc[2]};
   block_reduce<T, 3, false>(v, sred);

@@ -1,6 +1,7 @@
 // Host check of the float-float primitives used by the FP64-storage DHT
 // passes: conversions to and from FP64 by bit manipulation, and the
-// double-word sum and product, against long-double arithmetic.  Built and
+// double-word sum and product, against long-double arithmetic; and the
+// FP64 -> fixed-point conversion of the FP64 residual's linear part.  Built and
 // run by tests/test_ffloat.py (no GPU needed).  Exit status 0 = pass.
 #include <cfloat>
 #include <cmath>
@@ -86,6 +87,34 @@ int main() {
   for (int k = -120; k <= 120; ++k) {
     const double v = std::ldexp(1.0, k) * 3.0;
     if (psd::ff_to_double_bits(psd::ff_from_double_bits(v)) != v) ++fails;
+  }
+  // fixed point: round(v 2^S), ties away from zero, against long double
+  // (64-bit significand: v 2^S is exact there) and llroundl
+  {
+    int fx_fails = 0;
+    for (int t = 0; t < 200000; ++t) {
+      const int S = -40 + (int)(uniform() * 200.0);          // scales in [-40, 159]
+      const double v = rand_double(-70 - S, 60 - S);          // |v| 2^S in [2^-70, 2^61)
+      const long long want = llroundl(ldexpl((long double)v, S));
+      if (psd::fx_from_double(v, S) != want) ++fx_fails;
+    }
+    // ties (k + 1/2) 2^-S, both signs; zeros; subnormals; the largest values
+    for (int k = -1000; k <= 1000; ++k) {
+      const int S = 7 + (k & 31);
+      const double v = std::ldexp((double)k + 0.5, -S);
+      const long long want = k >= 0 ? (long long)k + 1 : (long long)k;  // away from zero
+      if (psd::fx_from_double(v, S) != want) ++fx_fails;
+    }
+    if (psd::fx_from_double(0.0, 55) != 0 || psd::fx_from_double(-0.0, 55) != 0) ++fx_fails;
+    if (psd::fx_from_double(std::ldexp(1.0, -1074), 1074) != 1) ++fx_fails;           // smallest subnormal
+    if (psd::fx_from_double(-std::ldexp(3.0, -1074), 1073) != -2) ++fx_fails;         // 1.5 -> 2
+    if (psd::fx_from_double(std::ldexp(1.0, -1074), 1000) != 0) ++fx_fails;
+    if (psd::fx_from_double(std::nextafter(std::ldexp(1.0, 8), 0.0), 53) != (1LL << 61) - 256) ++fx_fails;  // exact
+    if (psd::fx_from_double(-std::ldexp(1.0, 61), 0) != -(1LL << 61)) ++fx_fails;
+    for (int S = -200; S <= 200; ++S)
+      if (psd::fx_unit(S) != std::ldexp(1.0, -S)) ++fx_fails;
+    std::printf("fixed point: %d mismatches\n", fx_fails);
+    fails += fx_fails;
   }
   const double u2 = 0x1p-48;
   std::printf("split %.3g  roundtrip %.3g  to_double %.3g  add %.3g  mul %.3g  (units of 2^-48: %.2f %.2f %.2f %.2f %.2f)\n",

@@ -85,6 +85,53 @@ def test_residual_f32_kernel(oracle, shape):
     assert rel(host(r).astype(np.float64), ref) <= 2e-5
 
 
+@pytest.mark.parametrize("shape", [(16, 32, 64), (32, 32, 32), (64, 64, 128)])
+@pytest.mark.parametrize("order,s,eps", [(4, 0.1, 0.2), (4, 1.0, 0.01), (6, 0.1, 0.2)])
+def test_residual_fixed_point_parity(oracle, shape, order, s, eps):
+    """The outer-residual kernel variant of the mixed solve (linear part in
+    64-bit fixed point, p = 4 flux in float-float, final combination in FP64)
+    against the FP64 oracle, element by element; the (1.0, 0.01) case is
+    dominated by the flux part.  Order 6: the local part f - N_h^loc[u],
+    which is f - N6(u, g = u) (T_h[0] = 0)."""
+    P, h = _problem(oracle, order, shape, 4.0, s=s, eps=eps)
+    u = rng.standard_normal(shape) * 0.3
+    f = rng.standard_normal(shape)
+    S = Solver(order, shape, h, 4.0, P.s, P.eps, P.lam)
+    r = torch.empty(shape, dtype=torch.float64, device="cuda")
+    scale = S.residual_fixed(dev(u), dev(f), r)
+    e = int(np.frexp(np.max(np.abs(u)) * (1 + 2.0 ** -20))[1])
+    assert scale == 55 - e
+    ref = oracle.residual4(u, f, P) if order == 4 else f - oracle.N6(u, u, P)
+    assert rel(host(r), ref) <= 1e-12
+    r64 = torch.empty_like(r)
+    if order == 4:
+        S.residual(dev(u), dev(f), None, r64)
+        assert rel(host(r), host(r64)) <= 1e-12
+
+
+def test_residual_fixed_point_special_cases(oracle):
+    """u = 0 gives r = f exactly; |u| near 2^40 is the edge of the scale
+    range (S = 15 applies, S = 14 does not); p != 4 and 2D grids do not
+    take the variant (scale 0, r untouched)."""
+    shape = (16, 32, 64)
+    h = 2 * np.pi / shape[-1]
+    f = rng.standard_normal(shape)
+    S = Solver(4, shape, h, 4.0, 0.1, 0.2)
+    r = torch.empty(shape, dtype=torch.float64, device="cuda")
+    assert S.residual_fixed(dev(np.zeros(shape)), dev(f), r) == 55
+    assert np.array_equal(host(r), f)
+    base = rng.uniform(0.5, 0.9, shape)
+    assert S.residual_fixed(dev(base * 2.0 ** 40), dev(f), r) == 15  # max|u| in [2^39, 2^40)
+    assert S.residual_fixed(dev(base * 2.0 ** 41), dev(f), r) == 0
+    sentinel = torch.full(shape, 7.0, dtype=torch.float64, device="cuda")
+    S3 = Solver(4, shape, h, 3.0, 0.1, 0.2)
+    assert S3.residual_fixed(dev(base), dev(f), sentinel) == 0
+    S2 = Solver(4, (64, 64), h, 4.0, 0.1, 0.2)
+    s2 = torch.full((64, 64), 7.0, dtype=torch.float64, device="cuda")
+    assert S2.residual_fixed(dev(base[0, :64, :64]), dev(f[0, :64, :64]), s2) == 0
+    assert bool((sentinel == 7.0).all()) and bool((s2 == 7.0).all())
+
+
 # 8 x 8 x 8 CTAs of 32 x 32 x 16 cells: large enough for the register-blocked
 # FP32 residual kernel (which needs at least 2 x 152 such CTAs)
 RB_SHAPE = (128, 256, 256)

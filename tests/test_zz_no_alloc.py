@@ -5,8 +5,9 @@ allocator that refuses new allocations, plug-ins whose host owns every device
 allocation, fixed-budget deployments).  Its scratch is a static __device__
 array, so these tests check that it gives the same residual and norms as the
 handle-based psd_residual, on consecutive calls (the scratch keeps the last
-call's contents and must be cleared by each call), and that sizes beyond the
-array are refused.  The file is named so that pytest collects it last.
+call's contents and must be cleared by each call), including the grids that
+need the most residual blocks.  The file is named so that pytest collects it
+last.
 """
 
 import ctypes
@@ -20,7 +21,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_1607_01475_gb300 import PSDError, Solver, psd_residual_noalloc  # noqa: E402
+from paper_1607_01475_gb300 import Solver, psd_residual_noalloc  # noqa: E402
 from paper_1607_01475_gb300 import _lib  # noqa: E402
 
 
@@ -49,14 +50,24 @@ def test_noalloc_matches_handle_residual_on_consecutive_calls(shape, p):
     S.close()
 
 
-def test_noalloc_rejects_sizes_beyond_its_scratch():
-    shape = (8, 1024, 1024)  # needs 4096 residual blocks; the scratch holds 2048
-    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
-    r = torch.empty_like(u)
-    with pytest.raises(PSDError) as e:
-        psd_residual_noalloc(shape, 0.01, 4.0, 0.1, 0.1, u, u, r)
-    assert e.value.status == 1
-    assert "scratch" in str(e.value)
+@pytest.mark.parametrize("shape", [(1024, 1024, 16), (8, 1024, 1024), (1024, 1024)])
+def test_noalloc_accepts_the_grids_with_the_most_blocks(shape):
+    """The scratch holds 2048 residual blocks, and every valid grid fits:
+    (1024, 1024, 16) takes the small-tile 3D kernel with exactly 2048 blocks,
+    (8, 1024, 1024) the column kernel with one wave of blocks, 1024^2 the 2D
+    kernel with 1024 tiles.  Each agrees with the handle-based residual."""
+    rng = np.random.default_rng(12)
+    h = 2 * np.pi / shape[-1]
+    u = torch.from_numpy(rng.standard_normal(shape) * 0.3).cuda()
+    f = torch.from_numpy(rng.standard_normal(shape)).cuda()
+    S = Solver(4, shape, h, 4.0, 0.1, 0.2)
+    r_ref = torch.empty_like(u)
+    l2_ref, _ = S.residual(u, f, None, r_ref)
+    r = torch.full_like(u, float("nan"))
+    l2, _ = psd_residual_noalloc(shape, h, 4.0, 0.1, 0.2, u, f, r)
+    assert _rel(r.cpu().numpy(), r_ref.cpu().numpy()) <= 1e-12
+    assert abs(l2 - l2_ref) <= 1e-12 * l2_ref
+    S.close()
 
 
 def test_noalloc_rejects_sixth_order():
