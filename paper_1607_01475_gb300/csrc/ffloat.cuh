@@ -275,6 +275,64 @@ __host__ __device__ __forceinline__ long long fx_from_double(double v, int S) {
 // 2^-S as a double (|S| <= 1000), by bits
 __host__ __device__ __forceinline__ double fx_unit(int S) { return ff_bitsd((unsigned long long)(1023 - S) << 52); }
 
+// x 2^-S as a float-float, by integer operations only (|x| < 2^63,
+// 15 <= S <= 120, so that every exponent below is that of a normal float):
+// hi holds the leading 24 bits of |x|, lo the next 24 (both truncated), and a
+// fast two-sum normalises the pair; the relative error is below 2^-47.
+__host__ __device__ __forceinline__ int fx_clz64(unsigned long long a) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)a);
+#else
+  return __builtin_clzll(a);
+#endif
+}
+// x as a double, rounded to nearest (ties to even), by integer operations
+// only (|x| < 2^63): the same value as the hardware conversion.
+__host__ __device__ __forceinline__ double fx_to_double(long long x) {
+  if (x == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)x & (1ULL << 63);
+  const unsigned long long a = sgn ? 0ULL - (unsigned long long)x : (unsigned long long)x;
+  int e = 63 - fx_clz64(a);  // a in [2^e, 2^(e+1))
+  unsigned long long m;
+  if (e <= 52) {
+    m = a << (52 - e);
+  } else {
+    const int sh = e - 52;  // 1 .. 10
+    const unsigned long long rem = a & ((1ULL << sh) - 1ULL), half = 1ULL << (sh - 1);
+    m = a >> sh;
+    if (rem > half || (rem == half && (m & 1ULL))) ++m;
+    if (m >> 53) {  // rounding carried into a new leading bit
+      m >>= 1;
+      ++e;
+    }
+  }
+  return ff_bitsd(sgn | ((unsigned long long)(e + 1023) << 52) | (m & 0xFFFFFFFFFFFFFULL));
+}
+__host__ __device__ __forceinline__ ff fx_to_ff(long long x, int S) {
+  if (x == 0) return ff(0.0f, 0.0f);
+  const bool neg = x < 0;
+  const unsigned long long a = neg ? 0ULL - (unsigned long long)x : (unsigned long long)x;
+  const int e = 63 - fx_clz64(a);  // a in [2^e, 2^(e+1))
+  const int sh = e - 23;
+  const unsigned long long top = sh > 0 ? a >> sh : a << (-sh);
+  const unsigned long long rem = sh > 0 ? a - (top << sh) : 0ULL;  // < 2^sh
+  const float hi = ff_bitsf(((unsigned)(e - S + 127) << 23) | (unsigned)(top & 0x7FFFFFu));
+  float lo = 0.0f;
+  if (rem != 0) {
+    const int e2 = 63 - fx_clz64(rem);
+    const int sh2 = e2 - 23;
+    const unsigned long long top2 = sh2 > 0 ? rem >> sh2 : rem << (-sh2);
+    lo = ff_bitsf(((unsigned)(e2 - S + 127) << 23) | (unsigned)(top2 & 0x7FFFFFu));
+  }
+  ff z;
+  fast_two_sum(hi, lo, z.hi, z.lo);
+  if (neg) {
+    z.hi = -z.hi;
+    z.lo = -z.lo;
+  }
+  return z;
+}
+
 // Arithmetic operators so that the line-FFT templates run on ff (sums with
 // the butterfly-grade ff_add_fast).
 __host__ __device__ __forceinline__ ff operator+(ff a, ff b) { return ff_add_fast(a, b); }

@@ -40,10 +40,12 @@ namespace {
 // from a bound on |u| so that |q| <= 2^55), and the z-pair sums, vertex
 // gradients and both Laplacian passes are exact integer sums (|h^4 Delta_h^2
 // q| <= 144 2^55 < 2^63).  The flux part -- |G|^2 G, its z-sums S and the
-// divergence -- is evaluated in float-float from the exact gradients.  Only
-// r = (f - cu u) + (cdiv div - cbih bih) and the norms are FP64, so the
-// residual is that of u rounded to the grid 2^-S (at most 2^-56 max|u| away,
-// below the rounding of the FP64 Laplacian sums it replaces).  The caller
+// divergence -- is evaluated in float-float from the exact gradients
+// (converted by integer operations).  Only r = (f - cu u) + (cdiv div -
+// cbih bih) and the norms are FP64, with cu u from the FP64 u itself; the
+// flux and biharmonic terms are those of u rounded to the grid 2^-S (at
+// most 2^-56 max|u| away, below the rounding of the FP64 Laplacian sums they
+// replace).  The caller
 // selects it only when the worst-case float-float error of the flux part is
 // far below the solve tolerance (it scales with s q^4 max|G|^3).
 template <typename T, int PK, int MODE, bool FFX = false>
@@ -80,11 +82,10 @@ __global__ void __launch_bounds__(256, 2)
   const KConst<T>& C = kconst<T>(kp);
   const T cdiv = C.cdiv, cbih = C.cbih, cu = C.cu;
   const T beta = C.beta;
-  // fixed point (FFX): u = q 2^-S; the gradients enter the flux scaled by
-  // 2^-S (a float, S in [15, 120]); cu and cbih absorb 2^-S
+  // fixed point (FFX): u = q 2^-S (S in [15, 120]); the gradients enter the
+  // flux as float-float values of G 2^-S, cbih absorbs 2^-S
   const int fxs = FFX ? a.fxs : 0;
-  const float gsc = FFX ? __int_as_float((127 - fxs) << 23) : 1.0f;
-  const T cuq = FFX ? cu * (T)fx_unit(fxs) : cu, cbihq = FFX ? cbih * (T)fx_unit(fxs) : cbih;
+  const T cbihq = FFX ? cbih * (T)fx_unit(fxs) : cbih;
 
   // One wave of CTAs: the column-planes (w = column * nz + z, column = tile
   // index, x fastest) are split into equal contiguous shares, each marched
@@ -232,10 +233,8 @@ __global__ void __launch_bounds__(256, 2)
       G[1] = (sP[vy + 1][vx] - sP[vy][vx]) + (sP[vy + 1][vx + 1] - sP[vy][vx + 1]);
       G[2] = (sM[vy][vx] + sM[vy][vx + 1]) + (sM[vy + 1][vx] + sM[vy + 1][vx + 1]);
       if constexpr (FFX) {
-        // exact integer gradients -> float-float (within 2^-48), scaled by 2^-S
-        const ff g0 = ff_scale2(ff_from_double_bits(__ll2double_rn(G[0])), gsc);
-        const ff g1 = ff_scale2(ff_from_double_bits(__ll2double_rn(G[1])), gsc);
-        const ff g2 = ff_scale2(ff_from_double_bits(__ll2double_rn(G[2])), gsc);
+        // exact integer gradients -> float-float values of G 2^-S (within 2^-47)
+        const ff g0 = fx_to_ff(G[0], fxs), g1 = fx_to_ff(G[1], fxs), g2 = fx_to_ff(G[2], fxs);
         const ff q2 = ff_add_fast(ff_add_fast(g0 * g0, g1 * g1), g2 * g2);
         F[0] = q2 * g0;
         F[1] = q2 * g1;
@@ -313,6 +312,8 @@ __global__ void __launch_bounds__(256, 2)
     fetchU(z0 + 2);
     fetchB(z0 + 1);
     T fr = a.f ? a.f[(size_t)(z0 & (nz - 1)) * plane + gown] : T(0);
+    // FFX: the own cell's u in FP64 for the cu u term (the shared tile holds q)
+    T ur = FFX ? a.u_in[(size_t)(z0 & (nz - 1)) * plane + gown] : T(0);
 
     for (int z = z0; z < z0 + zc; ++z) {
       const int u2 = um;
@@ -320,10 +321,11 @@ __global__ void __launch_bounds__(256, 2)
       storeU(z + 2, u2);
       storeB(false);    // base P/M of plane z + 1/2
       __syncthreads();  // (A)
-      const T fcur = fr;
+      const T fcur = fr, ucur = ur;
       fetchU(z + 3);
       fetchB(z + 2);
       fr = a.f ? a.f[(size_t)((z + 1) & (nz - 1)) * plane + gown] : T(0);
+      if constexpr (FFX) ur = a.u_in[(size_t)((z + 1) & (nz - 1)) * plane + gown];
       const LT Lp = lap_plane(u0, u1, u2, lz ^ 1);  // lap'(z+1)
       phi_plane(false);                             // S/D for the cells of plane z
       const LT ucl = sU[u0][ty + 2][tx + 2];
@@ -331,12 +333,14 @@ __global__ void __launch_bounds__(256, 2)
       const LT bihl = (((sL[lz][ty + 1][tx] + sL[lz][ty + 1][tx + 2]) + (sL[lz][ty][tx + 1] + sL[lz][ty + 2][tx + 1])) +
                        (Lm + Lp)) -
                       LT(6) * L0;
-      // FFX: the integers in units of 2^-S (cuq, cbihq carry the factor)
+      // FFX: bih in units of 2^-S (cbihq carries the factor), u from FP64
       T uc, bih;
       if constexpr (FFX) {
-        uc = __ll2double_rn(ucl);
-        bih = __ll2double_rn(bihl);
+        (void)ucl;
+        uc = ucur;
+        bih = fx_to_double(bihl);
       } else {
+        (void)ucur;
         uc = ucl;
         bih = bihl;
       }
@@ -354,7 +358,7 @@ __global__ void __launch_bounds__(256, 2)
       else if (HVP)
         r = (cu * uc + cbih * bih) - cdiv * div;
       else
-        r = (fcur - cuq * uc) + (cdiv * div - cbihq * bih);
+        r = (fcur - cu * uc) + (cdiv * div - cbihq * bih);
       a.r[(size_t)(z & (nz - 1)) * plane + gown] = r;
       acc2 += HVP ? uc * r : r * r;
       accm = fmax(accm, fabs(r));

@@ -113,7 +113,42 @@ int main() {
     if (psd::fx_from_double(-std::ldexp(1.0, 61), 0) != -(1LL << 61)) ++fx_fails;
     for (int S = -200; S <= 200; ++S)
       if (psd::fx_unit(S) != std::ldexp(1.0, -S)) ++fx_fails;
-    std::printf("fixed point: %d mismatches\n", fx_fails);
+    // fixed point -> float-float: relative error below 2^-47, normalised,
+    // exact for values with at most 24 significant bits
+    double worst_fx = 0;
+    for (int t = 0; t < 200000; ++t) {
+      const int S = 15 + (int)(uniform() * 106.0);  // [15, 120]
+      const int bits = 1 + (int)(uniform() * 62.0);
+      long long x = (long long)(next_u64() >> (64 - bits));
+      if (next_u64() & 1) x = -x;
+      const ff z = psd::fx_to_ff(x, S);
+      if (!normalised(z)) ++fx_fails;
+      const long double ex = ldexpl((long double)x, -S);
+      if (x == 0) {
+        if (z.hi != 0.0f || z.lo != 0.0f) ++fx_fails;
+        continue;
+      }
+      const double r = (double)(std::fabs(exact(z) - ex) / std::fabs(ex));
+      if (r > worst_fx) worst_fx = r;
+      if (bits <= 24 && exact(z) != ex) ++fx_fails;
+    }
+    if (worst_fx > 0x1p-47) ++fx_fails;
+    // fixed point -> double: the same value as the C++ conversion (nearest, ties to even)
+    for (int t = 0; t < 200000; ++t) {
+      const int bits = 1 + (int)(uniform() * 62.0);
+      long long x = (long long)(next_u64() >> (64 - bits));
+      if (next_u64() & 1) x = -x;
+      if (psd::fx_to_double(x) != (double)x) ++fx_fails;
+    }
+    for (int k = 53; k <= 62; ++k) {  // ties at every shift: both even and odd neighbours
+      const long long base = 1LL << k, half = 1LL << (k - 53);
+      for (long long x : {base + half, base + 3 * half, base - 1, 0x7FFFFFFFFFFFFFFFLL})
+        if (psd::fx_to_double(x) != (double)x || psd::fx_to_double(-x) != (double)(-x)) ++fx_fails;
+    }
+    if (psd::fx_to_ff((1LL << 62) + 1, 62).hi != 1.0f) ++fx_fails;
+    if (psd::fx_to_ff(-(3LL << 40), 41).hi != -1.5f) ++fx_fails;
+    std::printf("fixed point: %d mismatches (to float-float: worst %.3g = %.2f units of 2^-48)\n", fx_fails,
+                worst_fx, worst_fx / 0x1p-48);
     fails += fx_fails;
   }
   const double u2 = 0x1p-48;
