@@ -39,15 +39,14 @@ __device__ __forceinline__ T vfactor(T g2, T beta) {
 template <int PK, typename T>
 __device__ __forceinline__ void flux_diff(const T (&a)[3], const T (&e)[3], T beta, T (&out)[3]) {
   const T a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
-  const T ae = a[0] * e[0] + a[1] * e[1] + a[2] * e[2];
-  const T e2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-  const T dl = T(2) * ae + e2;  // |a+e|^2 - |a|^2
+  // |a+e|^2 - |a|^2 = (2a + e).e, formed from e
+  const T dl = (T(2) * a[0] + e[0]) * e[0] + (T(2) * a[1] + e[1]) * e[1] + (T(2) * a[2] + e[2]) * e[2];
+  const T c2 = a2 + dl;  // |a+e|^2
   if (PK == PK_4) {
-    // |a+e|^2 (a+e) - |a|^2 a = |a|^2 e + (2 a.e + |e|^2)(a + e)
+    // |a+e|^2 (a+e) - |a|^2 a = |a+e|^2 e + (|a+e|^2 - |a|^2) a
 #pragma unroll
-    for (int c = 0; c < 3; ++c) out[c] = a2 * e[c] + dl * (a[c] + e[c]);
+    for (int c = 0; c < 3; ++c) out[c] = c2 * e[c] + dl * a[c];
   } else {
-    const T c2 = a2 + dl;
     const T fc = pow(c2 > T(0) ? c2 : T(0), beta);
     T dfac;  // |a+e|^{p-2} - |a|^{p-2}
     if (a2 > T(0))

@@ -178,10 +178,10 @@ __global__ void __launch_bounds__(256, 2)
     };
     // store the prefetched plane zz (own + halo) into its ring slot; the
     // updated own values go to u2 (and to u_out inside the block's z range)
-    auto storeU = [&](int zz) {
+    auto storeU = [&](int zz, int sl) {  // sl = slot(zz)
       const size_t gz = (size_t)(zz & (nz - 1)) * plane;
       const bool ownplane = zz >= z0 && zz < z0 + zc;
-      T(*S)[UX] = sU[slot(zz)];
+      T(*S)[UX] = sU[sl];
 #pragma unroll
       for (int i = 0; i < NY; ++i) {
         T v = pu[i];
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256, 2)
     // P/M of the vertex plane between U planes zl and zl+1 (own from the
     // registers ua, ub; ring from the U ring), and of the base field between
     // bprev and the prefetched base plane (first: only record)
-    auto storePM = [&](const T (&ua)[NY], const T (&ub)[NY], int zl) {
+    auto storePM = [&](const T (&ua)[NY], const T (&ub)[NY], int sa, int sb) {  // slots of zl, zl + 1
 #pragma unroll
       for (int i = 0; i < NY; ++i) {
         Po[i] = ua[i] + ub[i];
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256, 2)
         sM[cy0 + i + 1][tx + 1] = Mo[i];
       }
       if (rv) {
-        const T va = sU[slot(zl)][rly + 1][rlx + 1], vb = sU[slot(zl + 1)][rly + 1][rlx + 1];
+        const T va = sU[sa][rly + 1][rlx + 1], vb = sU[sb][rly + 1][rlx + 1];
         sP[rly][rlx] = va + vb;
         sM[rly][rlx] = vb - va;
       }
@@ -362,25 +362,25 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
     for (int i = 0; i < NY; ++i) um2[i] = upd ? pu[i] + alpha * pd[i] : pu[i];
     fetchU(z0 - 1);
-    storeU(z0 - 1);
+    storeU(z0 - 1, slot(z0 - 1));
 #pragma unroll
     for (int i = 0; i < NY; ++i) u1[i] = u2[i];  // u1 = U(z0-1) for now
     fetchU(z0);
-    storeU(z0);  // u2 = U(z0)
+    storeU(z0, slot(z0));  // u2 = U(z0)
     fetchB(z0 - 1);
     storeB(true);
     fetchB(z0);
     storeB(false);  // base P/M of vertex plane z0 - 1/2
     __syncthreads();
     lap_own(um2, u1, u2, slot(z0 - 1), Lm);  // lap'(z0-1)
-    storePM(u1, u2, z0 - 1);                  // P/M of vertex plane z0 - 1/2
+    storePM(u1, u2, slot(z0 - 1), slot(z0));  // P/M of vertex plane z0 - 1/2
 #pragma unroll
     for (int i = 0; i < NY; ++i) u0[i] = u2[i];  // u0 = U(z0)
     __syncthreads();
     phi_own(true);
     phi_halo(true);
     fetchU(z0 + 1);
-    storeU(z0 + 1);  // u2 = U(z0+1)
+    storeU(z0 + 1, slot(z0 + 1));  // u2 = U(z0+1)
 #pragma unroll
     for (int i = 0; i < NY; ++i) {
       um2[i] = u1[i];  // U(z0-1)
@@ -399,12 +399,13 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
     for (int i = 0; i < NY; ++i) pf[i] = a.f ? a.f[fz0 + ooff[i]] : T(0);
 
+    int s0 = 0, s1 = 1, s2 = 2;  // ring slots of U(z), U(z+1), U(z+2)
     for (int z = z0; z < z0 + zc; ++z) {
       // invariant: u0 = U(z), u1 = U(z+1); Lm = lap'(z-1), L0 = lap'(z) (own;
       // lap'(z) with halo in sL[lb]); Fo = flux at z - 1/2; U(z+2), B(z+1),
       // f(z) prefetched
-      storeU(z + 2);  // u2 = U(z+2)
-      storePM(u0, u1, z);
+      storeU(z + 2, s2);  // u2 = U(z+2)
+      storePM(u0, u1, s0, s1);
       storeB(false);
       T fcur[NY];
 #pragma unroll
@@ -418,10 +419,10 @@ __global__ void __launch_bounds__(256, 2)
         for (int i = 0; i < NY; ++i) pf[i] = a.f ? a.f[fz + ooff[i]] : T(0);
       }
       T Lp[NY];
-      lap_own(u0, u1, u2, slot(z + 1), Lp);  // lap'(z+1)
+      lap_own(u0, u1, u2, s1, Lp);  // lap'(z+1)
 #pragma unroll
       for (int i = 0; i < NY; ++i) sL[lb ^ 1][cy0 + i + 1][tx + 1] = Lp[i];
-      if (lv) sL[lb ^ 1][lly][llx] = lap_halo(lly, llx, slot(z), slot(z + 1), slot(z + 2));
+      if (lv) sL[lb ^ 1][lly][llx] = lap_halo(lly, llx, s0, s1, s2);
       phi_own(false);
       phi_halo(false);
       __syncthreads();  // (B)
@@ -473,6 +474,10 @@ __global__ void __launch_bounds__(256, 2)
         u1[i] = u2[i];
       }
       lb ^= 1;
+      const int st = s0;
+      s0 = s1;
+      s1 = s2;
+      s2 = st;
     }
     __syncthreads();  // the next segment's prologue refills the shared tiles
   }
