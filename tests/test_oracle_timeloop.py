@@ -1,0 +1,93 @@
+"""Pins of the oracle's thin-film time loop (Sec. 6.1, convex splitting),
+each independent of the loop's own code:
+
+* linear regime: for a small single Fourier mode the p-term is cubic in the
+  amplitude, so each step multiplies the mode by the closed-form factor
+  (1 + s mu_v) / (1 + s eps^2 mu^2), mu the symbol of -Delta_h and mu_v that
+  of the skew Laplacian -Delta_h^v (2D: (2/h^2)(1 - cos t_x cos t_y); 3D:
+  (4/h^2) sum_j sin^2(t_j/2) prod_{i != j} cos^2(t_i/2)).  Swapping Delta_h^v
+  for Delta_h, a sign, or the eps^2 factor changes the factor at the chosen
+  wave numbers by far more than the tolerance;
+* mass: every step preserves sum u (the right-hand side and N_h - I are
+  sums of differences);
+* energy: convex splitting never increases the discrete energy
+  h^d sum_v (1/p |grad u|^p - 1/2 |grad u|^2) + eps^2/2 ||Delta_h u||^2,
+  whatever the step s (checked at s = 0.1 h^2 and at s = 10 h^2);
+* the initial data of Eq. "init1" on (0, 3.2)^2 is sampled at cell centres.
+"""
+
+import numpy as np
+import pytest
+
+
+def _mode(shape, h, k, amp):
+    axes = [(np.arange(n) + 0.5) * h for n in shape]
+    grids = np.meshgrid(*axes, indexing="ij")
+    # array axis a is spatial axis a (any assignment works for a cosine mode)
+    phase = sum((2 * np.pi * kk / (n * h)) * g for kk, n, g in zip(k, shape, grids))
+    return amp * np.cos(phase)
+
+
+def _factor(shape, h, k, s, eps):
+    t = [2 * np.pi * kk / n for kk, n in zip(k, shape)]
+    mu = sum((4 / h ** 2) * np.sin(tt / 2) ** 2 for tt in t)
+    if len(shape) == 2:
+        mu_v = (2 / h ** 2) * (1 - np.cos(t[0]) * np.cos(t[1]))
+    else:
+        mu_v = 0.0
+        for j in range(3):
+            prod = 1.0
+            for i in range(3):
+                if i != j:
+                    prod *= np.cos(t[i] / 2) ** 2
+            mu_v += (4 / h ** 2) * np.sin(t[j] / 2) ** 2 * prod
+    return (1 + s * mu_v) / (1 + s * eps ** 2 * mu ** 2)
+
+
+@pytest.mark.parametrize("shape,k", [((16, 16), (3, 2)), ((16, 32), (1, 5)), ((8, 8, 16), (1, 2, 3))])
+def test_linear_regime_matches_closed_form(oracle, shape, k):
+    h = 0.2
+    s, eps = 0.3 * h ** 2, 0.1
+    P = oracle.Problem(4, h, 4.0, s, eps)
+    u0 = _mode(shape, h, k, 1e-6)
+    u, _ = oracle.thinfilm_steps(P, u0, 3, tol=1e-20, kmax=60)
+    g = _factor(shape, h, k, s, eps)
+    assert np.max(np.abs(u - g ** 3 * u0)) <= 1e-8 * np.max(np.abs(u0))
+    # the factor differs from the one with Delta_h in place of Delta_h^v
+    t = [2 * np.pi * kk / n for kk, n in zip(k, shape)]
+    mu = sum((4 / h ** 2) * np.sin(tt / 2) ** 2 for tt in t)
+    assert abs(g - (1 + s * mu) / (1 + s * eps ** 2 * mu ** 2)) > 1e-3
+
+
+def _init1(n):
+    L = 3.2
+    h = L / n
+    x = (np.arange(n) + 0.5) * h
+    y = x[:, None]
+    return (0.1 * np.sin(2 * np.pi * x / L) ** 2 * np.sin(4 * np.pi * (y - 1.4) / L)
+            - 0.1 * np.cos(2 * np.pi * (x - 2.0) / L) * np.sin(2 * np.pi * y / L)), h
+
+
+@pytest.mark.parametrize("p,s_over_h2", [(4.0, 0.1), (4.0, 10.0), (6.0, 0.1)])
+def test_mass_and_energy(oracle, p, s_over_h2):
+    u, h = _init1(16)
+    P = oracle.Problem(4, h, p, s_over_h2 * h * h, 0.1)
+    m0 = float(np.sum(u))
+    e = [oracle.thinfilm_energy(u, P)]
+    for _ in range(12):
+        u, _ = oracle.thinfilm_steps(P, u, 1, tol=1e-12)
+        e.append(oracle.thinfilm_energy(u, P))
+        assert abs(float(np.sum(u)) - m0) <= 1e-11 * max(1.0, abs(m0)) + 1e-11 * np.sum(np.abs(u))
+    de = np.diff(e)
+    assert np.all(de <= 1e-12 * np.max(np.abs(e))), de
+    assert e[-1] < e[0]
+
+
+def test_init1_sampling():
+    u, h = _init1(32)
+    assert h == pytest.approx(0.1)
+    # value at the first cell centre (0.05, 0.05), from the formula by hand
+    x = y = 0.05
+    ref = (0.1 * np.sin(2 * np.pi * x / 3.2) ** 2 * np.sin(4 * np.pi * (y - 1.4) / 3.2)
+           - 0.1 * np.cos(2 * np.pi * (x - 2.0) / 3.2) * np.sin(2 * np.pi * y / 3.2))
+    assert u[0, 0] == pytest.approx(ref, rel=1e-15)
