@@ -173,6 +173,19 @@ psd_status psd_set_history(psd_handle h, double* alpha_hist, double* res_hist,
 psd_status psd_residual_f32(psd_handle h, const float* u, const float* f,
                             float* r);
 
+/* Thin-film epitaxy time loop (Sec. 6.1, Eq. "thin-film-fully-discrete"):
+ * nsteps steps of the convex-splitting scheme N_h[u^{n+1}] = u^n -
+ * s Delta_h^v u^n with the handle's fourth-order operator (s is the time
+ * step), each solve started from u^n and run like psd_solve (the handle's
+ * precision and tolerance).  u: device, N doubles, u^0 in, u^{nsteps} out.
+ * info (host, may be NULL): iters and outer_iters summed over the steps,
+ * res_l2, res_linf, last_alpha and status of the last solve, wall_ms of the
+ * whole loop (CUDA events).  Stops at the first step whose solve fails and
+ * returns its status.  Errors: PSD_ERR_INVALID for a null u, nsteps < 0 or
+ * a sixth-order handle.                                                     */
+psd_status psd_thinfilm_steps(psd_handle h, double* u, int nsteps,
+                              psd_info* info);
+
 /* FP64 residual by the kernel variant of the mixed solve's outer residual,
  * for tests: r = f - N_h[u] (order 6: the local part, without T_h) with the
  * linear part (z-pair sums, vertex gradients, both Laplacian passes of

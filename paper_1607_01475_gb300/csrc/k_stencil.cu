@@ -777,6 +777,41 @@ __global__ void k_accumulate_f64(double* u, const float* delta, float* u32, size
   }
 }
 
+// Thin-film right-hand side f = u - s Delta_h^v u (Sec. 6.1, Eq.
+// "thin-film-fully-discrete"), one cell per thread, FP64.  The skew
+// Laplacian is sum_a d_a D_a with D_a and d_a the vertex difference
+// operators of Sec. 5.1 (3D: the tensor extension), i.e. along each axis
+// the second difference (1, -2, 1) times the average (1, 2, 1)/4 along the
+// other axes: integer weights 2 (corners) and -8 (centre) over 4 h^2 in 2D;
+// 3 (corners), 2 (edges), -4 (faces), -24 (centre) over 16 h^2 in 3D.
+__global__ void __launch_bounds__(NT) k_thinfilm_rhs(const double* __restrict__ u, double* __restrict__ f,
+                                                     KParams kp) {
+  const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+  const size_t plane = (size_t)nx * ny, n = plane * nz;
+  const double sc = kp.s * kp.inv_h * kp.inv_h * (kp.dim == 3 ? 1.0 / 16.0 : 0.25);
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / plane);
+    double acc = 0.0;
+    if (kp.dim == 2) {
+      const int xm = (x - 1) & (nx - 1), xp = (x + 1) & (nx - 1);
+      const int ym = (y - 1) & (ny - 1), yp = (y + 1) & (ny - 1);
+      acc = 2.0 * ((u[(size_t)ym * nx + xm] + u[(size_t)ym * nx + xp]) + (u[(size_t)yp * nx + xm] + u[(size_t)yp * nx + xp])) -
+            8.0 * u[i];
+    } else {
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int k = (dx != 0) + (dy != 0) + (dz != 0);  // 0 centre, 1 face, 2 edge, 3 corner
+            const double w = k == 0 ? -24.0 : (k == 1 ? -4.0 : (k == 2 ? 2.0 : 3.0));
+            const size_t j = (size_t)((z + dz) & (nz - 1)) * plane + (size_t)((y + dy) & (ny - 1)) * nx +
+                             (size_t)((x + dx) & (nx - 1));
+            acc += w * u[j];
+          }
+    }
+    f[i] = u[i] - sc * acc;
+  }
+}
+
 // sum x (y + z) (z may be null) -> c->rd
 __global__ void __launch_bounds__(NT) k_dot(const double* x, const double* y, const double* z, size_t n, Ctrl* c,
                                             double* partials) {
@@ -944,6 +979,11 @@ cudaError_t launch_dot(const double* x, const double* y, const double* z, size_t
 cudaError_t launch_gradmax(const float* u, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st) {
   const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
   k_gradmax<<<std::min(grid1d(n), 1024), NT, 0, st>>>(u, kp, ctrl, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_thinfilm_rhs(const double* u, double* f, const KParams& kp, cudaStream_t st) {
+  const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
+  k_thinfilm_rhs<<<grid1d(n), NT, 0, st>>>(u, f, kp);
   return cudaGetLastError();
 }
 cudaError_t launch_energy_terms(const double* u, const double* f, double gbar, const KParams& kp, Ctrl* ctrl,

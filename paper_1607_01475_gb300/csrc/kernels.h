@@ -107,6 +107,9 @@ cudaError_t launch_linesearch(const T* u, const T* ubase, const T* d, int pk, co
 // FP32 field u (g = q G), into ctrl->res_linf (an estimate for choosing the
 // float-float flux of the FP64 residual).  3D grids with nx >= 32, ny >= 8.
 cudaError_t launch_gradmax(const float* u, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st);
+// Right-hand side of the thin-film convex-splitting step (Sec. 6.1):
+// f = u - s Delta_h^v u (FP64, 2D and 3D).
+cudaError_t launch_thinfilm_rhs(const double* u, double* f, const KParams& kp, cudaStream_t st);
 
 // Local sums of the discrete energy of u (FP64) into ctrl->rd, dd, lapdd,
 // tdd: sum (u - f)^2 (order 4) or sum u^2 (order 6); sum (u - gbar) f

@@ -62,6 +62,7 @@ struct psd_context {
   double* D = nullptr;      // search direction
   double* Z = nullptr;      // order 6: plain solve: xi = -DHT(u - g)/mu; mixed: DHT(u - g)
   double* Dsp = nullptr;    // order 6: DHT spectrum of T_h d for the last direction d
+  double* Ftf = nullptr;    // thin-film time loop: right-hand side of the current step
   // FP32 work arrays (mixed)
   float* u32 = nullptr;
   float* da = nullptr;
@@ -853,7 +854,7 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
 
 psd_status psd_destroy(psd_handle c) {
   if (!c) return PSD_OK;
-  void* ptrs[] = {c->tables, c->ub, c->W, c->D, c->Z, c->Dsp, c->u32, c->da, c->db, c->W32, c->D32,
+  void* ptrs[] = {c->tables, c->ub, c->W, c->D, c->Z, c->Dsp, c->Ftf, c->u32, c->da, c->db, c->W32, c->D32,
                   c->R32, c->Dsp32, c->partials, c->ctrl, c->ctrl2, c->d_hist};
   for (void* p : ptrs) dev_free(c, p);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
@@ -1186,6 +1187,51 @@ psd_status psd_solve(psd_handle c, const double* f, const double* g, double* u, 
   if (c->prm.report_energy && info) TRY(compute_energy(c, u, f, g, &info->energy));
   if (s != PSD_OK)
     fail(c, s, std::string("solve ended with ") + psd_status_string(s));
+  return s;
+}
+
+psd_status psd_thinfilm_steps(psd_handle c, double* u, int nsteps, psd_info* info) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u || nsteps < 0) return fail(c, PSD_ERR_INVALID, "u is required and nsteps must be >= 0");
+  if (c->prm.order != 4) return fail(c, PSD_ERR_INVALID, "the thin-film time loop needs a fourth-order handle");
+  TRY(alloc(c, &c->Ftf, c->N));
+  psd_info acc{};
+  acc.status = PSD_OK;
+  // own events: every psd_solve records the handle's ev0 / ev1
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  CK(cudaEventCreate(&t0));
+  if (cudaEventCreate(&t1) != cudaSuccess) {
+    cudaEventDestroy(t0);
+    return fail(c, PSD_ERR_CUDA, "cudaEventCreate failed");
+  }
+  struct Events {
+    cudaEvent_t a, b;
+    ~Events() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev_guard{t0, t1};
+  CK(cudaEventRecord(t0, c->st));
+  psd_status s = PSD_OK;
+  for (int n = 0; n < nsteps; ++n) {
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_thinfilm_rhs(u, c->Ftf, c->kp, c->st)); }
+    psd_info one{};
+    s = psd_solve(c, c->Ftf, nullptr, u, nullptr, &one);
+    acc.iters += one.iters;
+    acc.outer_iters += one.outer_iters;
+    acc.res_l2 = one.res_l2;
+    acc.res_linf = one.res_linf;
+    acc.energy = one.energy;
+    acc.last_alpha = one.last_alpha;
+    acc.status = one.status;
+    if (s != PSD_OK) break;
+  }
+  CK(cudaEventRecord(t1, c->st));
+  CK(cudaEventSynchronize(t1));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, t0, t1));
+  acc.wall_ms = ms;
+  if (info) *info = acc;
   return s;
 }
 

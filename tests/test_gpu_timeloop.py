@@ -1,0 +1,80 @@
+"""The thin-film convex-splitting time loop (Sec. 6.1) through
+psd_thinfilm_steps against the oracle's loop (thinfilm_steps), element by
+element after the same number of steps: the initial data of Eq. "init1" on
+(0, 3.2)^2 with s = 0.1 h^2 and eps = 0.1 (the parameters printed with
+Table 1), p = 4 and 6, FP64 and mixed precision; and a smooth 3D field.
+Every solve stops at ||r||_2 < 1e-12 on both sides, and the slow growth of
+the unstable modes over a few dozen steps keeps the difference near 1e-10
+of |u|."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1607_01475_gb300 import PSD_FP64, PSD_MIXED, PSDError, Solver, synthetic  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _init1(n):
+    L = 3.2
+    h = L / n
+    x = (np.arange(n) + 0.5) * h
+    y = x[:, None]
+    return (0.1 * np.sin(2 * np.pi * x / L) ** 2 * np.sin(4 * np.pi * (y - 1.4) / L)
+            - 0.1 * np.cos(2 * np.pi * (x - 2.0) / L) * np.sin(2 * np.pi * y / L)), h
+
+
+@pytest.mark.parametrize("n,p,nsteps", [(16, 4.0, 20), (32, 4.0, 40), (32, 6.0, 20)])
+@pytest.mark.parametrize("precision", [PSD_FP64, PSD_MIXED])
+def test_thinfilm_steps_match_oracle(oracle, n, p, nsteps, precision):
+    u0, h = _init1(n)
+    s, eps = 0.1 * h * h, 0.1
+    P = oracle.Problem(4, h, p, s, eps)
+    ref, _ = oracle.thinfilm_steps(P, u0, nsteps, tol=1e-12)
+    S = Solver(4, (n, n), h, p, s, eps, precision=precision, tol=1e-12)
+    u = dev(u0)
+    info = S.thinfilm_steps(u, nsteps)
+    got = u.cpu().numpy()
+    assert info["status"] == 0 and info["res_l2"] < 1e-12
+    assert info["iters"] >= nsteps and info["wall_ms"] > 0
+    assert rel(got, ref) <= 1e-8
+    assert abs(got.sum() - u0.sum()) <= 1e-10 * np.abs(u0).sum()
+
+
+def test_thinfilm_steps_3d(oracle):
+    shape = (16, 16, 32)
+    h = 2 * np.pi / 32
+    u0 = 0.05 * synthetic.fourier_field(shape, 2 * np.pi, 4, 77, nmodes=16)
+    s, eps = 0.1 * h * h, 0.1
+    P = oracle.Problem(4, h, 4.0, s, eps)
+    ref, _ = oracle.thinfilm_steps(P, u0, 6, tol=1e-12)
+    S = Solver(4, shape, h, 4.0, s, eps, precision=PSD_MIXED, tol=1e-12)
+    u = dev(u0)
+    info = S.thinfilm_steps(u, 6)
+    assert info["status"] == 0
+    assert rel(u.cpu().numpy(), ref) <= 1e-8
+
+
+def test_thinfilm_steps_arguments():
+    u0, h = _init1(16)
+    S = Solver(4, (16, 16), h, 4.0, 0.1 * h * h, 0.1)
+    u = dev(u0)
+    info = S.thinfilm_steps(u, 0)
+    assert info["iters"] == 0 and np.array_equal(u.cpu().numpy(), u0)
+    with pytest.raises(PSDError):
+        S.thinfilm_steps(u, -1)
+    S6 = Solver(6, (16, 16), h, 4.0, 0.1, 0.1, 1.0)
+    with pytest.raises(PSDError):
+        S6.thinfilm_steps(u, 1)
