@@ -56,7 +56,7 @@ __all__ = [
     "N4", "residual4", "energy4", "second_variation4", "precond4",
     "T_h", "N6", "residual6", "energy6", "second_variation6", "precond6",
     "recover_w", "line_search", "psd_solve", "Problem", "hvp4", "dN4_ds", "adjoint4",
-    "thinfilm_rhs", "thinfilm_energy", "thinfilm_steps",
+    "thinfilm_rhs", "thinfilm_energy", "thinfilm_steps", "spfc_rhs", "spfc_energy", "spfc_steps",
 ]
 
 
@@ -587,5 +587,42 @@ def thinfilm_steps(P, u0, nsteps, tol=1e-12, kmax=1000):
     iters = []
     for _ in range(nsteps):
         u, info = psd_solve(P, thinfilm_rhs(u, P), u, tol=tol, kmax=kmax)
+        iters.append(info["iters"])
+    return u, iters
+
+
+# --------------------------------------------------------------------------
+# Square phase field crystal (SPFC), convex-splitting time loop (Sec. 6.2,
+# Eq. "scheme-spfc"; the s-scaled right-hand side of the scheme in Sec. 1):
+# each step solves the sixth-order problem of Sec. 5.4 with lambda = gamma_0,
+# g = u^n and f = -s gamma_1 Delta_h u^n.
+# --------------------------------------------------------------------------
+
+def spfc_rhs(u, P, gamma1):
+    """(f, g) = (-s gamma_1 Delta_h u^n, u^n)."""
+    return -P.s * gamma1 * lap(u, P.h), u.copy()
+
+
+def spfc_energy(u, P, gamma1):
+    """Discrete SPFC energy (Sec. 6.2 with the operators of Sec. 5.1):
+    gamma_0/2 ||u||^2 + gamma_1/2 (u, Delta_h u)_2 + eps^2/2 ||Delta_h u||^2
+    + 1/4 h^d sum_v |grad_h^v u|^4, gamma_0 = lambda.  The convex-splitting
+    scheme does not increase it, for any step s."""
+    h = P.h
+    lu = lap(u, h)
+    g = vgrad(u, h)
+    g2 = sum(c * c for c in g)
+    return (0.5 * P.lam * ip2(u, u, h) + 0.5 * gamma1 * ip2(u, lu, h) + 0.5 * P.eps ** 2 * ip2(lu, lu, h)
+            + 0.25 * h ** u.ndim * float(np.sum(g2 * g2)))
+
+
+def spfc_steps(P, u0, gamma1, nsteps, tol=1e-12, kmax=1000):
+    """nsteps SPFC steps from u0 (order 6, p = 4), each PSD solve started
+    from the previous step's solution; returns (u, per-step iterations)."""
+    u = np.array(u0, dtype=np.float64, copy=True)
+    iters = []
+    for _ in range(nsteps):
+        f, g = spfc_rhs(u, P, gamma1)
+        u, info = psd_solve(P, f, u, g=g, tol=tol, kmax=kmax)
         iters.append(info["iters"])
     return u, iters

@@ -91,3 +91,49 @@ def test_init1_sampling():
     ref = (0.1 * np.sin(2 * np.pi * x / 3.2) ** 2 * np.sin(4 * np.pi * (y - 1.4) / 3.2)
            - 0.1 * np.cos(2 * np.pi * (x - 2.0) / 3.2) * np.sin(2 * np.pi * y / 3.2))
     assert u[0, 0] == pytest.approx(ref, rel=1e-15)
+
+
+# ------------------------------------------------------------------ SPFC
+# Sec. 6.2: order 6 with lambda = gamma_0, g = u^n, f = -s gamma_1 Delta_h u^n.
+# A small mode on a constant background is multiplied per step by
+# (1 + s gamma_1 mu^2) / (1 + s gamma_0 mu + s eps^2 mu^3) (the T_h term
+# contributes 1/mu times the difference to the previous step); the mean of u
+# is that of g = u^n, so it never changes.
+
+def _spfc_factor(shape, h, k, s, eps, g0, g1):
+    t = [2 * np.pi * kk / n for kk, n in zip(k, shape)]
+    mu = sum((4 / h ** 2) * np.sin(tt / 2) ** 2 for tt in t)
+    return (1 + s * g1 * mu ** 2) / (1 + s * g0 * mu + s * eps ** 2 * mu ** 3)
+
+
+@pytest.mark.parametrize("shape,k", [((16, 16), (3, 2)), ((8, 8, 16), (1, 2, 3))])
+def test_spfc_linear_regime_matches_closed_form(oracle, shape, k):
+    h, s, eps, g0, g1 = 1.25, 0.5, 1.0, 0.5, 2.0
+    P = oracle.Problem(6, h, 4.0, s, eps, g0)
+    u0 = 0.3 + _mode(shape, h, k, 1e-6)
+    u, _ = oracle.spfc_steps(P, u0, g1, 3, tol=1e-14, kmax=80)
+    G = _spfc_factor(shape, h, k, s, eps, g0, g1)
+    assert abs(G - 1.0) > 0.05
+    assert np.max(np.abs(u - (0.3 + G ** 3 * (u0 - 0.3)))) <= 1e-8 * 1e-6
+    # a missing s on the right-hand side (the printed Sec. 6.2 form) gives another factor
+    t = [2 * np.pi * kk / n for kk, n in zip(k, shape)]
+    mu = sum((4 / h ** 2) * np.sin(tt / 2) ** 2 for tt in t)
+    assert abs(G - (1 + g1 * mu ** 2) / (1 + s * g0 * mu + s * eps ** 2 * mu ** 3)) > 0.05
+
+
+@pytest.mark.parametrize("s", [0.01, 1.0])
+def test_spfc_mass_and_energy(oracle, s):
+    rng = np.random.default_rng(5)
+    n, L = 16, 20.0
+    h = L / n
+    u = 0.2 + 0.05 * (2 * rng.random((n, n)) - 1)  # the shape of Eq. "init2" around a mean
+    P = oracle.Problem(6, h, 4.0, s, 1.0, 0.5)
+    m0 = float(u.mean())
+    e = [oracle.spfc_energy(u, P, 2.0)]
+    for _ in range(8):
+        u, _ = oracle.spfc_steps(P, u, 2.0, 1, tol=1e-12)
+        e.append(oracle.spfc_energy(u, P, 2.0))
+        assert abs(float(u.mean()) - m0) <= 1e-13
+    de = np.diff(e)
+    assert np.all(de <= 1e-12 * np.max(np.abs(e))), de
+    assert e[-1] < e[0]
