@@ -186,6 +186,15 @@ psd_status psd_residual_f32(psd_handle h, const float* u, const float* f,
 psd_status psd_thinfilm_steps(psd_handle h, double* u, int nsteps,
                               psd_info* info);
 
+/* Square phase field crystal time loop (Sec. 6.2, Eq. "scheme-spfc", with
+ * the s-scaled explicit term of the scheme in Sec. 1): nsteps steps of the
+ * sixth-order problem of Sec. 5.4 (lambda of the handle = gamma_0, p = 4
+ * expected) with g = u^n and f = -s gamma1 Delta_h u^n, each solve started
+ * from u^n.  mean(u) is kept.  u, info and errors as psd_thinfilm_steps,
+ * for a sixth-order handle; gamma1 >= 0, finite.                           */
+psd_status psd_spfc_steps(psd_handle h, double* u, double gamma1, int nsteps,
+                          psd_info* info);
+
 /* FP64 residual by the kernel variant of the mixed solve's outer residual,
  * for tests: r = f - N_h[u] (order 6: the local part, without T_h) with the
  * linear part (z-pair sums, vertex gradients, both Laplacian passes of

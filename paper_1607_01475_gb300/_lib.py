@@ -90,6 +90,7 @@ def load_library(build_if_missing=True):
     lib.psd_residual_f32.argtypes = [H, F, F, F]
     lib.psd_residual_fixed.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_int)]
     lib.psd_thinfilm_steps.argtypes = [H, D, ctypes.c_int, ctypes.POINTER(PSDInfo)]
+    lib.psd_spfc_steps.argtypes = [H, D, ctypes.c_double, ctypes.c_int, ctypes.POINTER(PSDInfo)]
     lib.psd_precond_solve_f32.argtypes = [H, F, F]
     lib.psd_energy.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.psd_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
@@ -113,7 +114,7 @@ def load_library(build_if_missing=True):
     lib.psd_status_string.argtypes = [ctypes.c_int]
     lib.psd_status_string.restype = ctypes.c_char_p
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
-                 "psd_set_history", "psd_residual_f32", "psd_residual_fixed", "psd_thinfilm_steps", "psd_last_error",
+                 "psd_set_history", "psd_residual_f32", "psd_residual_fixed", "psd_thinfilm_steps", "psd_spfc_steps", "psd_last_error",
                  "psd_profile",
                  "psd_profile_read", "psd_profile_classes", "psd_residual_noalloc", "psd_noalloc_last_error",
                  "psd_precond_solve_f32", "psd_energy",
@@ -243,6 +244,16 @@ def psd_thinfilm_steps(handle, u, nsteps, allow_noconv=False):
     return info.as_dict()
 
 
+def psd_spfc_steps(handle, u, gamma1, nsteps, allow_noconv=False):
+    """nsteps SPFC convex-splitting steps in place on u (see include/psd.h);
+    returns the accumulated info as a dict."""
+    info = PSDInfo()
+    allow = (4,) if allow_noconv else ()
+    _check(load_library().psd_spfc_steps(handle, _ptr(u), float(gamma1), int(nsteps), ctypes.byref(info)), handle,
+           allow)
+    return info.as_dict()
+
+
 def psd_residual_fixed(handle, u, f, r):
     """FP64 residual by the fixed-point / float-float kernel variant; returns
     the fixed-point scale S (0: the variant does not apply, r untouched)."""
@@ -359,6 +370,9 @@ class Solver:
 
     def thinfilm_steps(self, u, nsteps):
         return psd_thinfilm_steps(self.handle, u, nsteps)
+
+    def spfc_steps(self, u, gamma1, nsteps):
+        return psd_spfc_steps(self.handle, u, gamma1, nsteps)
 
     def precond_solve_f32(self, r, d):
         psd_precond_solve_f32(self.handle, r, d)

@@ -812,6 +812,31 @@ __global__ void __launch_bounds__(NT) k_thinfilm_rhs(const double* __restrict__ 
   }
 }
 
+// SPFC right-hand side (Sec. 6.2, Eq. "scheme-spfc", with the s-scaled
+// explicit term of the scheme in Sec. 1): f = -c Delta_h u, c = s gamma_1,
+// Delta_h the 5- or 7-point Laplacian; g = u.  One cell per thread, FP64.
+__global__ void __launch_bounds__(NT) k_spfc_rhs(const double* __restrict__ u, double* __restrict__ f,
+                                                 double* __restrict__ g, double c, KParams kp) {
+  const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+  const size_t plane = (size_t)nx * ny, n = plane * nz;
+  const double sc = c * kp.inv_h * kp.inv_h;
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / plane);
+    const size_t row = i - x, pl = (size_t)z * plane;
+    const double uc = u[i];
+    double sum = (u[row + ((x + 1) & (nx - 1))] + u[row + ((x - 1) & (nx - 1))]) +
+                 (u[pl + (size_t)((y + 1) & (ny - 1)) * nx + x] + u[pl + (size_t)((y - 1) & (ny - 1)) * nx + x]);
+    double cw = 4.0;
+    if (kp.dim == 3) {
+      const size_t xy = i - pl;
+      sum += u[(size_t)((z + 1) & (nz - 1)) * plane + xy] + u[(size_t)((z - 1) & (nz - 1)) * plane + xy];
+      cw = 6.0;
+    }
+    f[i] = -sc * (sum - cw * uc);
+    g[i] = uc;
+  }
+}
+
 // sum x (y + z) (z may be null) -> c->rd
 __global__ void __launch_bounds__(NT) k_dot(const double* x, const double* y, const double* z, size_t n, Ctrl* c,
                                             double* partials) {
@@ -984,6 +1009,11 @@ cudaError_t launch_gradmax(const float* u, const KParams& kp, Ctrl* ctrl, double
 cudaError_t launch_thinfilm_rhs(const double* u, double* f, const KParams& kp, cudaStream_t st) {
   const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
   k_thinfilm_rhs<<<grid1d(n), NT, 0, st>>>(u, f, kp);
+  return cudaGetLastError();
+}
+cudaError_t launch_spfc_rhs(const double* u, double* f, double* g, double c, const KParams& kp, cudaStream_t st) {
+  const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
+  k_spfc_rhs<<<grid1d(n), NT, 0, st>>>(u, f, g, c, kp);
   return cudaGetLastError();
 }
 cudaError_t launch_energy_terms(const double* u, const double* f, double gbar, const KParams& kp, Ctrl* ctrl,

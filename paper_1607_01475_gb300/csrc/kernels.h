@@ -110,6 +110,9 @@ cudaError_t launch_gradmax(const float* u, const KParams& kp, Ctrl* ctrl, double
 // Right-hand side of the thin-film convex-splitting step (Sec. 6.1):
 // f = u - s Delta_h^v u (FP64, 2D and 3D).
 cudaError_t launch_thinfilm_rhs(const double* u, double* f, const KParams& kp, cudaStream_t st);
+// Right-hand side of the SPFC convex-splitting step (Sec. 6.2):
+// f = -c Delta_h u (c = s gamma_1), g = u (FP64, 2D and 3D).
+cudaError_t launch_spfc_rhs(const double* u, double* f, double* g, double c, const KParams& kp, cudaStream_t st);
 
 // Local sums of the discrete energy of u (FP64) into ctrl->rd, dd, lapdd,
 // tdd: sum (u - f)^2 (order 4) or sum u^2 (order 6); sum (u - gbar) f

@@ -62,7 +62,8 @@ struct psd_context {
   double* D = nullptr;      // search direction
   double* Z = nullptr;      // order 6: plain solve: xi = -DHT(u - g)/mu; mixed: DHT(u - g)
   double* Dsp = nullptr;    // order 6: DHT spectrum of T_h d for the last direction d
-  double* Ftf = nullptr;    // thin-film time loop: right-hand side of the current step
+  double* Ftf = nullptr;    // time loops: right-hand side f of the current step
+  double* Gtf = nullptr;    // SPFC time loop: g = u^n of the current step
   // FP32 work arrays (mixed)
   float* u32 = nullptr;
   float* da = nullptr;
@@ -854,7 +855,7 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
 
 psd_status psd_destroy(psd_handle c) {
   if (!c) return PSD_OK;
-  void* ptrs[] = {c->tables, c->ub, c->W, c->D, c->Z, c->Dsp, c->Ftf, c->u32, c->da, c->db, c->W32, c->D32,
+  void* ptrs[] = {c->tables, c->ub, c->W, c->D, c->Z, c->Dsp, c->Ftf, c->Gtf, c->u32, c->da, c->db, c->W32, c->D32,
                   c->R32, c->Dsp32, c->partials, c->ctrl, c->ctrl2, c->d_hist};
   for (void* p : ptrs) dev_free(c, p);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
@@ -1190,11 +1191,13 @@ psd_status psd_solve(psd_handle c, const double* f, const double* g, double* u, 
   return s;
 }
 
-psd_status psd_thinfilm_steps(psd_handle c, double* u, int nsteps, psd_info* info) {
-  if (!c) return PSD_ERR_INVALID;
-  if (!u || nsteps < 0) return fail(c, PSD_ERR_INVALID, "u is required and nsteps must be >= 0");
-  if (c->prm.order != 4) return fail(c, PSD_ERR_INVALID, "the thin-film time loop needs a fourth-order handle");
-  TRY(alloc(c, &c->Ftf, c->N));
+}  // extern "C"
+
+namespace {
+// Time loop shared by the thin-film and SPFC schemes: per step, rhs() forms
+// the right-hand side(s) from u^n, then psd_solve runs from u^n.
+template <typename Rhs>
+psd_status run_steps(psd_context* c, double* u, int nsteps, psd_info* info, const double* g, Rhs&& rhs) {
   psd_info acc{};
   acc.status = PSD_OK;
   // own events: every psd_solve records the handle's ev0 / ev1
@@ -1214,9 +1217,9 @@ psd_status psd_thinfilm_steps(psd_handle c, double* u, int nsteps, psd_info* inf
   CK(cudaEventRecord(t0, c->st));
   psd_status s = PSD_OK;
   for (int n = 0; n < nsteps; ++n) {
-    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_thinfilm_rhs(u, c->Ftf, c->kp, c->st)); }
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(rhs()); }
     psd_info one{};
-    s = psd_solve(c, c->Ftf, nullptr, u, nullptr, &one);
+    s = psd_solve(c, c->Ftf, g, u, nullptr, &one);
     acc.iters += one.iters;
     acc.outer_iters += one.outer_iters;
     acc.res_l2 = one.res_l2;
@@ -1233,6 +1236,29 @@ psd_status psd_thinfilm_steps(psd_handle c, double* u, int nsteps, psd_info* inf
   acc.wall_ms = ms;
   if (info) *info = acc;
   return s;
+}
+}  // namespace
+
+extern "C" {
+
+psd_status psd_thinfilm_steps(psd_handle c, double* u, int nsteps, psd_info* info) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u || nsteps < 0) return fail(c, PSD_ERR_INVALID, "u is required and nsteps must be >= 0");
+  if (c->prm.order != 4) return fail(c, PSD_ERR_INVALID, "the thin-film time loop needs a fourth-order handle");
+  TRY(alloc(c, &c->Ftf, c->N));
+  return run_steps(c, u, nsteps, info, nullptr, [&]() { return psd::launch_thinfilm_rhs(u, c->Ftf, c->kp, c->st); });
+}
+
+psd_status psd_spfc_steps(psd_handle c, double* u, double gamma1, int nsteps, psd_info* info) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u || nsteps < 0) return fail(c, PSD_ERR_INVALID, "u is required and nsteps must be >= 0");
+  if (c->prm.order != 6) return fail(c, PSD_ERR_INVALID, "the SPFC time loop needs a sixth-order handle");
+  if (!(gamma1 >= 0.0) || !std::isfinite(gamma1)) return fail(c, PSD_ERR_INVALID, "gamma1 must be finite and >= 0");
+  TRY(alloc(c, &c->Ftf, c->N));
+  TRY(alloc(c, &c->Gtf, c->N));
+  const double cf = c->kp.s * gamma1;
+  return run_steps(c, u, nsteps, info, c->Gtf,
+                   [&]() { return psd::launch_spfc_rhs(u, c->Ftf, c->Gtf, cf, c->kp, c->st); });
 }
 
 psd_status psd_energy(psd_handle c, const double* u, const double* f, const double* g, double* energy) {

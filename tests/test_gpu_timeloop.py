@@ -78,3 +78,38 @@ def test_thinfilm_steps_arguments():
     S6 = Solver(6, (16, 16), h, 4.0, 0.1, 0.1, 1.0)
     with pytest.raises(PSDError):
         S6.thinfilm_steps(u, 1)
+
+
+# ------------------------------------------------------------------ SPFC
+
+@pytest.mark.parametrize("shape,nsteps", [((32, 32), 10), ((16, 16, 16), 4)])
+@pytest.mark.parametrize("precision", [PSD_FP64, PSD_MIXED])
+def test_spfc_steps_match_oracle(oracle, shape, nsteps, precision):
+    """SPFC steps (Sec. 6.2: eps = 1, gamma_0 = lambda = 0.5, gamma_1 = 2)
+    from random data of the shape of Eq. "init2" around a mean, against the
+    oracle's loop; the mean of u is kept."""
+    rng = np.random.default_rng(9)
+    L = 20.0
+    h = L / shape[-1]
+    s, eps, g0, g1 = 0.1, 1.0, 0.5, 2.0
+    u0 = 0.2 + 0.05 * (2 * rng.random(shape) - 1)
+    P = oracle.Problem(6, h, 4.0, s, eps, g0)
+    ref, _ = oracle.spfc_steps(P, u0, g1, nsteps, tol=1e-12)
+    S = Solver(6, shape, h, 4.0, s, eps, g0, precision=precision, tol=1e-12)
+    u = dev(u0)
+    info = S.spfc_steps(u, g1, nsteps)
+    got = u.cpu().numpy()
+    assert info["status"] == 0
+    assert rel(got - u0.mean(), ref - u0.mean()) <= 1e-8
+    assert abs(got.mean() - u0.mean()) <= 1e-13
+
+
+def test_spfc_steps_arguments():
+    S4 = Solver(4, (16, 16), 0.1, 4.0, 0.1, 0.1)
+    u = torch.zeros((16, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(PSDError):
+        S4.spfc_steps(u, 2.0, 1)
+    S6 = Solver(6, (16, 16), 0.5, 4.0, 0.1, 1.0, 0.5)
+    with pytest.raises(PSDError):
+        S6.spfc_steps(u, -1.0, 1)
+    assert S6.spfc_steps(u, 2.0, 0)["iters"] == 0
