@@ -256,8 +256,10 @@ const char* psd_profile_class_name(int k);
  * precision are ignored.  u, f, r: device arrays as for psd_residual (r is
  * required); res_l2 / res_linf: host pointers or NULL.  Synchronises the
  * stream.  Returns PSD_ERR_INVALID for a bad size or parameter, including
- * grids whose residual launch needs more than 2048 blocks (beyond 256^3 in
- * 3D; every 2D size up to 1024^2 fits).  All calls share the scratch: calls
+ * grids whose residual launch needs more than 2048 blocks (none of the
+ * valid sizes on a device with up to 1024 SMs: 3D grids run one wave of at
+ * most 2 blocks per SM, 2D grids at most 1024 tiles, 3D grids with
+ * nx < 32 at most 2048 blocks).  All calls share the scratch: calls
  * that overlap on the GPU race.  The first call on a device looks up the
  * scratch address; make it before any stream capture.                    */
 psd_status psd_residual_noalloc(const psd_params* params, const double* u,
