@@ -126,9 +126,14 @@ def algorithmic_bytes_per_cell(cls, order):
 
 
 def kernel_source_hash():
+    """Hash of the device-code sources (the k_*.cu kernel files and the
+    headers they include); the host drivers (psd_api.cu, psd_batch.cu,
+    psd_noalloc.cu) define no kernels and are left out."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1607_01475_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
+        if not (name.endswith((".cuh", ".h")) or (name.startswith("k_") and name.endswith(".cu"))):
+            continue
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
