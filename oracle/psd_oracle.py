@@ -56,7 +56,8 @@ __all__ = [
     "N4", "residual4", "energy4", "second_variation4", "precond4",
     "T_h", "N6", "residual6", "energy6", "second_variation6", "precond6",
     "recover_w", "line_search", "psd_solve", "Problem", "hvp4", "dN4_ds", "adjoint4",
-    "thinfilm_rhs", "thinfilm_energy", "thinfilm_steps", "spfc_rhs", "spfc_energy", "spfc_steps",
+    "thinfilm_rhs", "thinfilm_energy", "thinfilm_steps", "thinfilm_adjoint",
+    "spfc_rhs", "spfc_energy", "spfc_steps",
 ]
 
 
@@ -626,3 +627,25 @@ def spfc_steps(P, u0, gamma1, nsteps, tol=1e-12, kmax=1000):
         u, info = psd_solve(P, f, u, g=g, tol=tol, kmax=kmax)
         iters.append(info["iters"])
     return u, iters
+
+
+def thinfilm_adjoint(P, u0, nsteps, grad_uN, tol=1e-13):
+    """Gradient of a loss J(u^N) of the thin-film time loop with respect to
+    u^0 and s (Euclidean, like adjoint4), given dJ/du^N.  Not in the paper:
+    the chain rule through the steps of Sec. 6.1.  Step n maps u^n to the
+    solution u^{n+1} of N_h[u] = f_n, f_n = u^n - s Delta_h^v u^n; with
+    mu_n = H(u^{n+1})^{-1} lambda_{n+1} (adjoint4, dJ/df_n = mu_n):
+      lambda_n = mu_n - s Delta_h^v mu_n          (Delta_h^v is symmetric)
+      dJ/ds   += -(mu_n . dN_h/ds(u^{n+1})) - (mu_n . Delta_h^v u^n).
+    Returns (dJ/du^0, dJ/ds); every forward state is kept."""
+    us = [np.array(u0, dtype=np.float64, copy=True)]
+    for _ in range(nsteps):
+        u, _ = psd_solve(P, thinfilm_rhs(us[-1], P), us[-1], tol=tol, kmax=2000)
+        us.append(u)
+    lam = np.array(grad_uN, dtype=np.float64, copy=True)
+    gs = 0.0
+    for n in reversed(range(nsteps)):
+        mu, gs_n, _ = adjoint4(us[n + 1], lam, P, tol=tol)
+        gs += gs_n - float(np.sum(mu * skew_lap(us[n], P.h)))
+        lam = mu - P.s * skew_lap(mu, P.h)
+    return lam, gs

@@ -137,3 +137,40 @@ def test_spfc_mass_and_energy(oracle, s):
     de = np.diff(e)
     assert np.all(de <= 1e-12 * np.max(np.abs(e))), de
     assert e[-1] < e[0]
+
+
+# ------------------------------------------------ adjoint through the loop
+
+def test_thinfilm_adjoint_matches_finite_differences(oracle):
+    """dJ/du^0 and dJ/ds of J = 1/2 |u^N - target|^2 through 3 thin-film
+    steps against central differences of J (step 1e-5, solves to 1e-14):
+    both agree to about 1e-9; leaving out the right-hand side's dependence
+    on s (the -Delta_h^v u^n term) changes dJ/ds by far more."""
+    rng = np.random.default_rng(1)
+    n, h, s, eps, N = 8, 0.4, 0.05, 0.3, 3
+    P = oracle.Problem(4, h, 4.0, s, eps)
+    u0 = 0.3 * rng.standard_normal((n, n))
+    tgt = 0.2 * rng.standard_normal((n, n))
+    v = rng.standard_normal((n, n))
+
+    def J(u_init, s_=s):
+        u, _ = oracle.thinfilm_steps(oracle.Problem(4, h, 4.0, s_, eps), u_init, N, tol=1e-14, kmax=3000)
+        return 0.5 * float(np.sum((u - tgt) ** 2)), u
+
+    _, uN = J(u0)
+    gu, gs = oracle.thinfilm_adjoint(P, u0, N, uN - tgt, tol=1e-14)
+    e = 1e-5
+    fd_u = (J(u0 + e * v)[0] - J(u0 - e * v)[0]) / (2 * e)
+    fd_s = (J(u0, s * (1 + e))[0] - J(u0, s * (1 - e))[0]) / (2 * e * s)
+    assert abs(float(np.sum(gu * v)) - fd_u) <= 1e-7 * abs(fd_u)
+    assert abs(gs - fd_s) <= 1e-7 * abs(fd_s)
+    # the s-dependence of the right-hand side matters
+    us = [u0]
+    for _ in range(N):
+        us.append(oracle.thinfilm_steps(P, us[-1], 1, tol=1e-14, kmax=3000)[0])
+    lam, rhs_part = uN - tgt, 0.0
+    for k in reversed(range(N)):
+        mu, _, _ = oracle.adjoint4(us[k + 1], lam, P, tol=1e-14)
+        rhs_part -= float(np.sum(mu * oracle.skew_lap(us[k], h)))
+        lam = mu - s * oracle.skew_lap(mu, h)
+    assert abs(rhs_part) > 1e-3 * abs(fd_s)
