@@ -186,6 +186,28 @@ psd_status psd_residual_f32(psd_handle h, const float* u, const float* f,
 psd_status psd_thinfilm_steps(psd_handle h, double* u, int nsteps,
                               psd_info* info);
 
+/* Gradient of a loss J(u^N) of the thin-film time loop with respect to the
+ * initial state u^0 and to s (order 4; entrywise, like psd_adjoint).  Not in
+ * the paper: the chain rule backwards through the steps of
+ * psd_thinfilm_steps.  With mu_n = H(u^{n+1})^{-1} lambda_{n+1} (one
+ * psd_adjoint solve per step, tol_rel and max_iter as there):
+ * lambda_n = mu_n - s Delta_h^v mu_n, and grad_s collects
+ * -(mu_n . dN_h/ds(u^{n+1})) - (mu_n . Delta_h^v u^n).  The forward states
+ * are recomputed from checkpoints: every K-th state is kept (K =
+ * ceil(nsteps / checkpoints); checkpoints <= 0 selects ceil(sqrt(nsteps))),
+ * and each segment is recomputed once on the way back, so the workspace is
+ * about (checkpoints + K + 5) N doubles, allocated for the call (through
+ * the allocator callback if set) and released before it returns.
+ * u0, grad_uN (= dJ/du^N): device inputs; grad_u0: device output;
+ * grad_s: host double or NULL.  info (host, may be NULL): iters = adjoint
+ * CG iterations, outer_iters = forward PSD iterations (the recomputation
+ * included), wall_ms.  Errors: PSD_ERR_INVALID (null pointers, nsteps < 0,
+ * max_iter < 1, a sixth-order handle); the status of a failing solve.     */
+psd_status psd_thinfilm_adjoint(psd_handle h, const double* u0, int nsteps,
+                                const double* grad_uN, double* grad_u0,
+                                double* grad_s, int checkpoints,
+                                double tol_rel, int max_iter, psd_info* info);
+
 /* Square phase field crystal time loop (Sec. 6.2, Eq. "scheme-spfc", with
  * the s-scaled explicit term of the scheme in Sec. 1): nsteps steps of the
  * sixth-order problem of Sec. 5.4 (lambda of the handle = gamma_0, p = 4

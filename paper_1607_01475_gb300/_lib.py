@@ -91,6 +91,8 @@ def load_library(build_if_missing=True):
     lib.psd_residual_fixed.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_int)]
     lib.psd_thinfilm_steps.argtypes = [H, D, ctypes.c_int, ctypes.POINTER(PSDInfo)]
     lib.psd_spfc_steps.argtypes = [H, D, ctypes.c_double, ctypes.c_int, ctypes.POINTER(PSDInfo)]
+    lib.psd_thinfilm_adjoint.argtypes = [H, D, ctypes.c_int, D, D, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, ctypes.POINTER(PSDInfo)]
     lib.psd_precond_solve_f32.argtypes = [H, F, F]
     lib.psd_energy.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.psd_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
@@ -114,7 +116,7 @@ def load_library(build_if_missing=True):
     lib.psd_status_string.argtypes = [ctypes.c_int]
     lib.psd_status_string.restype = ctypes.c_char_p
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
-                 "psd_set_history", "psd_residual_f32", "psd_residual_fixed", "psd_thinfilm_steps", "psd_spfc_steps", "psd_last_error",
+                 "psd_set_history", "psd_residual_f32", "psd_residual_fixed", "psd_thinfilm_steps", "psd_spfc_steps", "psd_thinfilm_adjoint", "psd_last_error",
                  "psd_profile",
                  "psd_profile_read", "psd_profile_classes", "psd_residual_noalloc", "psd_noalloc_last_error",
                  "psd_precond_solve_f32", "psd_energy",
@@ -254,6 +256,17 @@ def psd_spfc_steps(handle, u, gamma1, nsteps, allow_noconv=False):
     return info.as_dict()
 
 
+def psd_thinfilm_adjoint(handle, u0, nsteps, grad_uN, grad_u0, checkpoints=0, tol_rel=1e-12, max_iter=1000):
+    """grad_u0 <- dJ/du^0 through nsteps thin-film steps from u0, given
+    grad_uN = dJ/du^N (see include/psd.h); returns (dJ/ds, info)."""
+    gs = ctypes.c_double()
+    info = PSDInfo()
+    _check(load_library().psd_thinfilm_adjoint(handle, _ptr(u0), int(nsteps), _ptr(grad_uN), _ptr(grad_u0),
+                                                ctypes.byref(gs), int(checkpoints), float(tol_rel), int(max_iter),
+                                                ctypes.byref(info)), handle)
+    return gs.value, info.as_dict()
+
+
 def psd_residual_fixed(handle, u, f, r):
     """FP64 residual by the fixed-point / float-float kernel variant; returns
     the fixed-point scale S (0: the variant does not apply, r untouched)."""
@@ -373,6 +386,9 @@ class Solver:
 
     def spfc_steps(self, u, gamma1, nsteps):
         return psd_spfc_steps(self.handle, u, gamma1, nsteps)
+
+    def thinfilm_adjoint(self, u0, nsteps, grad_uN, grad_u0, checkpoints=0, tol_rel=1e-12, max_iter=1000):
+        return psd_thinfilm_adjoint(self.handle, u0, nsteps, grad_uN, grad_u0, checkpoints, tol_rel, max_iter)
 
     def precond_solve_f32(self, r, d):
         psd_precond_solve_f32(self.handle, r, d)

@@ -1261,6 +1261,115 @@ psd_status psd_spfc_steps(psd_handle c, double* u, double gamma1, int nsteps, ps
                    [&]() { return psd::launch_spfc_rhs(u, c->Ftf, c->Gtf, cf, c->kp, c->st); });
 }
 
+psd_status psd_thinfilm_adjoint(psd_handle c, const double* u0, int nsteps, const double* grad_uN, double* grad_u0,
+                                double* grad_s, int checkpoints, double tol_rel, int max_iter, psd_info* info) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!u0 || !grad_uN || !grad_u0 || nsteps < 0)
+    return fail(c, PSD_ERR_INVALID, "u0, grad_uN and grad_u0 are required and nsteps must be >= 0");
+  if (c->prm.order != 4) return fail(c, PSD_ERR_INVALID, "the thin-film adjoint needs a fourth-order handle");
+  if (max_iter < 1) return fail(c, PSD_ERR_INVALID, "max_iter must be >= 1");
+  const size_t N = c->N, bytes = N * sizeof(double);
+  const int ncp = checkpoints > 0 ? std::min(checkpoints, std::max(nsteps, 1))
+                                  : std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
+  const int K = nsteps > 0 ? (nsteps + ncp - 1) / ncp : 1;  // steps per segment
+  const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+  // workspace, released on return: the checkpoints u^{jK}, the states of one
+  // segment, lambda, mu and a temporary
+  struct Work {
+    psd_context* c;
+    double* p[5];
+    ~Work() {
+      for (double* q : p) dev_free(c, q);
+    }
+  } w{c, {nullptr, nullptr, nullptr, nullptr, nullptr}};
+  TRY(alloc(c, &w.p[0], (size_t)std::max(nseg, 1) * N));
+  TRY(alloc(c, &w.p[1], (size_t)(K + 1) * N));
+  TRY(alloc(c, &w.p[2], N));
+  TRY(alloc(c, &w.p[3], N));
+  TRY(alloc(c, &w.p[4], N));
+  TRY(alloc(c, &c->Ftf, N));
+  double *ck = w.p[0], *seg = w.p[1], *lam = w.p[2], *mu = w.p[3], *tmp = w.p[4];
+  const KParams& kp = c->kp;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  CK(cudaEventCreate(&t0));
+  if (cudaEventCreate(&t1) != cudaSuccess) {
+    cudaEventDestroy(t0);
+    return fail(c, PSD_ERR_CUDA, "cudaEventCreate failed");
+  }
+  struct Events {
+    cudaEvent_t a, b;
+    ~Events() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev_guard{t0, t1};
+  CK(cudaEventRecord(t0, c->st));
+  int fwd_iters = 0, adj_iters = 0;
+  auto step = [&](double* u) -> psd_status {  // one thin-film step in place
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_thinfilm_rhs(u, c->Ftf, kp, c->st)); }
+    psd_info one{};
+    const psd_status s = psd_solve(c, c->Ftf, nullptr, u, nullptr, &one);
+    fwd_iters += one.iters;
+    return s;
+  };
+  // forward: record u^{jK}; the last segment is recomputed by the backward pass
+  CK(cudaMemcpyAsync(seg, u0, bytes, cudaMemcpyDeviceToDevice, c->st));
+  for (int j = 0; j < nseg; ++j) {
+    CK(cudaMemcpyAsync(ck + (size_t)j * N, seg, bytes, cudaMemcpyDeviceToDevice, c->st));
+    if (j == nseg - 1) break;
+    for (int t = 0; t < K; ++t) TRY(step(seg));
+  }
+  // backward: lambda_N = grad_uN; per step mu = H(u^{n+1})^{-1} lambda,
+  // dJ/ds += -(mu . dN/ds) - (mu . Delta_h^v u^n), lambda = mu - s Delta_h^v mu
+  CK(cudaMemcpyAsync(lam, grad_uN, bytes, cudaMemcpyDeviceToDevice, c->st));
+  double gs = 0.0;
+  for (int j = nseg - 1; j >= 0; --j) {
+    const int len = std::min(K, nsteps - j * K);
+    CK(cudaMemcpyAsync(seg, ck + (size_t)j * N, bytes, cudaMemcpyDeviceToDevice, c->st));
+    for (int t = 1; t <= len; ++t) {
+      double* ut = seg + (size_t)t * N;
+      CK(cudaMemcpyAsync(ut, ut - N, bytes, cudaMemcpyDeviceToDevice, c->st));
+      TRY(step(ut));
+    }
+    for (int t = len - 1; t >= 0; --t) {
+      double* un = seg + (size_t)t * N;
+      double gs_n = 0.0;
+      psd_info ai{};
+      TRY(psd_adjoint(c, un + N, lam, mu, &gs_n, tol_rel, max_iter, &ai));
+      adj_iters += ai.iters;
+      gs += gs_n;
+      // -(mu . Delta_h^v u^n) = (mu . (u^n - s Delta_h^v u^n - u^n)) / s
+      Ctrl h0;
+      init_ctrl(h0, -1.0, 1 << 30);
+      TRY(upload_ctrl(c, c->ctrl2, h0));
+      {
+        ProfScope p_(c, PSD_PROF_OTHER);
+        CK(psd::launch_thinfilm_rhs(un, tmp, kp, c->st));
+        CK(psd::launch_axpby<double>(tmp, tmp, un, 1.0, -1.0, 0.0, N, c->st));
+        CK(psd::launch_dot(mu, tmp, nullptr, N, c->ctrl2, c->partials, c->st));
+      }
+      Ctrl hd;
+      TRY(read_ctrl(c, c->ctrl2, hd));
+      gs += hd.rd / kp.s;
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_thinfilm_rhs(mu, lam, kp, c->st)); }
+    }
+  }
+  CK(cudaMemcpyAsync(grad_u0, lam, bytes, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaEventRecord(t1, c->st));
+  CK(cudaEventSynchronize(t1));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, t0, t1));
+  if (grad_s) *grad_s = gs;
+  if (info) {
+    *info = psd_info{};
+    info->iters = adj_iters;
+    info->outer_iters = fwd_iters;
+    info->wall_ms = ms;
+    info->status = PSD_OK;
+  }
+  return PSD_OK;
+}
+
 psd_status psd_energy(psd_handle c, const double* u, const double* f, const double* g, double* energy) {
   if (!c) return PSD_ERR_INVALID;
   if (!u || !f || !energy) return fail(c, PSD_ERR_INVALID, "u, f and energy are required");

@@ -113,3 +113,40 @@ def test_spfc_steps_arguments():
     with pytest.raises(PSDError):
         S6.spfc_steps(u, -1.0, 1)
     assert S6.spfc_steps(u, 2.0, 0)["iters"] == 0
+
+
+# -------------------------------------------------- adjoint through the loop
+
+@pytest.mark.parametrize("checkpoints", [0, 1, 2, 6])
+def test_thinfilm_adjoint_matches_oracle(oracle, checkpoints):
+    """dJ/du^0 and dJ/ds through 6 thin-film steps (J = 1/2 |u^N - target|^2)
+    against the oracle's backward recursion (itself pinned by finite
+    differences); the checkpoint count changes only the recomputation, so
+    every setting gives the same bits."""
+    rng = np.random.default_rng(4)
+    n, h, s, eps, N = 16, 0.4, 0.05, 0.3, 6
+    P = oracle.Problem(4, h, 4.0, s, eps)
+    u0 = 0.3 * rng.standard_normal((n, n))
+    tgt = 0.2 * rng.standard_normal((n, n))
+    uN, _ = oracle.thinfilm_steps(P, u0, N, tol=1e-13)
+    ref_u, ref_s = oracle.thinfilm_adjoint(P, u0, N, uN - tgt, tol=1e-13)
+    S = Solver(4, (n, n), h, 4.0, s, eps, tol=1e-13)
+    u = dev(u0)
+    S.thinfilm_steps(u, N)
+    gu0 = torch.empty_like(u)
+    gs, info = S.thinfilm_adjoint(dev(u0), N, u - dev(tgt), gu0, checkpoints=checkpoints, tol_rel=1e-13)
+    assert info["status"] == 0 and info["iters"] > 0
+    assert rel(gu0.cpu().numpy(), ref_u) <= 1e-8
+    assert abs(gs - ref_s) <= 1e-8 * abs(ref_s)
+    if checkpoints == 6:
+        g2 = torch.empty_like(u)
+        gs2, _ = S.thinfilm_adjoint(dev(u0), N, u - dev(tgt), g2, checkpoints=1, tol_rel=1e-13)
+        assert torch.equal(g2, gu0) and gs2 == gs
+
+
+def test_thinfilm_adjoint_zero_steps_is_identity():
+    S = Solver(4, (16, 16), 0.4, 4.0, 0.05, 0.3)
+    g = torch.randn((16, 16), dtype=torch.float64, device="cuda")
+    out = torch.empty_like(g)
+    gs, _ = S.thinfilm_adjoint(torch.zeros_like(g), 0, g, out)
+    assert torch.equal(out, g) and gs == 0.0
