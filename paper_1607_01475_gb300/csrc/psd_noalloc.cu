@@ -32,7 +32,7 @@
 
 namespace {
 
-constexpr int kMaxBlocks = 2048;  // residual blocks (256^3 in 3D, 1024^2 in 2D)
+constexpr int kMaxBlocks = 2048;  // residual blocks: every valid grid needs at most 2048 on up to 1024 SMs
 constexpr size_t kCtrlBytes = (sizeof(psd::Ctrl) + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kCtrlBytes + (size_t)kMaxBlocks * 2 * sizeof(double);
 constexpr int kMaxDevices = 64;
