@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -62,7 +63,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the samples go to $PSD_CLOCKS_DIR (default: the system temp directory)
+        out = os.environ.get("PSD_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"psd_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:

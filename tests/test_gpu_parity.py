@@ -5,8 +5,7 @@ Tolerances (relative L-infinity, max|a - b| / max|b|):
   evaluate the same sums in a different order; each output is a sum of at
   most ~30 terms whose magnitude is bounded by ~100x the result on these
   inputs, so rounding differences stay below ~1e-13.
-* converged FP64 solutions: 1e-11 (the spec bar), both sides iterated
-  to the FP64 floor.
+* converged FP64 solutions: 1e-11, both sides iterated to the FP64 floor.
 * mixed precision after the outer FP64 correction: 1e-9.
 """
 
