@@ -55,7 +55,7 @@ __all__ = [
     "ip2", "ipv", "norm2", "mu_symbol",
     "N4", "residual4", "energy4", "second_variation4", "precond4",
     "T_h", "N6", "residual6", "energy6", "second_variation6", "precond6",
-    "recover_w", "line_search", "psd_solve", "Problem", "hvp4", "dN4_ds", "adjoint4",
+    "recover_w", "line_search", "line_search_poly", "psd_solve", "Problem", "hvp4", "dN4_ds", "adjoint4",
     "thinfilm_rhs", "thinfilm_energy", "thinfilm_steps", "thinfilm_adjoint",
     "spfc_rhs", "spfc_energy", "spfc_steps",
 ]
@@ -431,6 +431,42 @@ def line_search(q, dq, alpha0, max_iter=200):
             return new
         alpha = new
     return alpha
+
+
+def line_search_poly(u, d, f, P, g=None):
+    """Coefficients (lowest power first) of q(alpha) = (N_h[u + alpha d] - f, d)_2
+    for even p = 2, 4, 6, where q is a polynomial of degree p - 1 (Sec. 6.1:
+    a cubic for p = 4, a quintic for p = 6).  The linear part of N_h gives
+    (Lin u - f, d)_2 + alpha (Lin d, d)_2 (order 6: T_h[u - g] in Lin u, T_h d
+    in Lin d); by summation by parts the p-term is
+    s <|a + alpha b|^{p-2} (a + alpha b), b> with a = grad_h^v u and
+    b = grad_h^v d at the vertices, expanded in A = |a|^2, B = a.b, C = |b|^2."""
+    if P.p not in (2.0, 4.0, 6.0):
+        raise ValueError("q is a polynomial for even p only")
+    h = P.h
+    s, se2 = P.s, P.s * P.eps ** 2
+    if P.order == 4:
+        lin_u = u + se2 * lap(lap(u, h), h)
+        lin_d = d + se2 * lap(lap(d, h), h)
+    else:
+        lin_u = s * P.lam * u + se2 * lap(lap(u, h), h) + T_h(u - g, h)
+        lin_d = s * P.lam * d + se2 * lap(lap(d, h), h) + T_h(d, h)
+    ga, gb = vgrad(u, h), vgrad(d, h)
+    A = sum(c * c for c in ga)
+    B = sum(x * y for x, y in zip(ga, gb))
+    C = sum(c * c for c in gb)
+    if P.p == 2.0:
+        terms = [B, C]
+    elif P.p == 4.0:
+        terms = [A * B, A * C + 2 * B * B, 3 * B * C, C * C]
+    else:
+        terms = [A * A * B, A * A * C + 4 * A * B * B, 6 * A * B * C + 4 * B ** 3,
+                 8 * B * B * C + 2 * A * C * C, 5 * B * C * C, C ** 3]
+    w = s * h ** u.ndim
+    coef = [w * float(np.sum(t)) for t in terms]
+    coef[0] += ip2(lin_u - f, d, h)
+    coef[1] += ip2(lin_d, d, h)
+    return coef
 
 
 # --------------------------------------------------------------------------

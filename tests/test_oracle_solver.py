@@ -288,3 +288,34 @@ def test_preconditioner_inverts_stencil_operator(oracle, shape):
     Ld6 = (s * lam * d6 - s * oracle.lap(d6, h) + s * eps ** 2 * oracle.lap(oracle.lap(d6, h), h)
            + oracle.T_h(d6, h))
     np.testing.assert_allclose(Ld6, r - r.mean(), atol=1e-11)
+
+
+@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("p", [2.0, 4.0, 6.0])
+@pytest.mark.parametrize("shape", [(16, 16), (8, 8, 8)])
+def test_line_search_polynomial(oracle, order, p, shape):
+    """q(alpha) = (N_h[u + alpha d] - f, d)_2 is a polynomial of degree p - 1
+    for even p (Sec. 6.1: a cubic for p = 4, a quintic for p = 6); the
+    oracle's coefficients reproduce the literal q at seven step sizes, and a
+    perturbed coefficient would not."""
+    h = 0.3
+    P = oracle.Problem(order, h, p, 0.1, 0.4, 0.7)
+    u = 0.5 * rng.standard_normal(shape)
+    d = 0.5 * rng.standard_normal(shape)
+    f = rng.standard_normal(shape)
+    g = rng.standard_normal(shape) if order == 6 else None
+
+    def q(al):
+        v = u + al * d
+        nv = oracle.N4(v, P) if order == 4 else oracle.N6(v, g, P)
+        return oracle.ip2(nv - f, d, h)
+
+    c = oracle.line_search_poly(u, d, f, P, g)
+    assert len(c) == int(p)
+    alphas = (-1.3, -0.4, 0.0, 0.2, 0.7, 1.5, 2.2)
+    qs = [q(al) for al in alphas]
+    scale = max(abs(x) for x in qs)
+    for al, qa in zip(alphas, qs):
+        assert abs(sum(ck * al ** k for k, ck in enumerate(c)) - qa) <= 1e-12 * scale
+    # the top coefficient is s <|b|^p> > 0 and matters at these step sizes
+    assert c[-1] > 0 and abs(c[-1]) * 2.2 ** (len(c) - 1) > 1e-6 * scale
