@@ -319,7 +319,10 @@ class Batch:
             raise PSDError(st, buf.value.decode())
         self.handle = out
 
-    def solve(self, fs, us, gs=None, allow_noconv=False):
+    def solve(self, fs, us, gs=None, allow_noconv=False, check=True):
+        """Solve every instance; returns the per-instance info dicts.  With
+        check=False a failing batch does not raise: (status, message, infos)
+        is returned instead, so that the other instances can be inspected."""
         lib = load_library()
         P = ctypes.c_void_p * self.n
         fp = P(*[_ptr(t).value for t in fs])
@@ -327,10 +330,15 @@ class Batch:
         gp = P(*[(_ptr(t).value if t is not None else None) for t in gs]) if gs is not None else None
         infos = (PSDInfo * self.n)()
         st = lib.psd_batch_solve(self.handle, fp, gp, up, infos)
-        if st != 0 and not (allow_noconv and st == 4):
+        msg = ""
+        if st != 0:
             buf = ctypes.create_string_buffer(512)
             lib.psd_batch_last_error(self.handle, buf, len(buf))
-            raise PSDError(st, buf.value.decode())
+            msg = buf.value.decode()
+        if not check:
+            return st, msg, [i.as_dict() for i in infos]
+        if st != 0 and not (allow_noconv and st == 4):
+            raise PSDError(st, msg)
         return [i.as_dict() for i in infos]
 
     def close(self):

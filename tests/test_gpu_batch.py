@@ -72,3 +72,21 @@ def test_batch_workload_96_instances(oracle):
         P = oracle.Problem(4, w["L"] / w["shape"][-1], w["p"], w["s"], w["eps"])
         r = oracle.residual4(us[k].cpu().numpy(), w["f"], P)
         assert oracle.norm2(r, P.h) < 1.05 * w["tol"] + 1e-12, k
+
+
+def test_batch_poisoned_instance_fails_alone():
+    """Fault injection on the host: one instance's f carries a NaN.  That
+    instance reports PSD_ERR_NONFINITE (7), the batch returns that status and
+    names the instance, and every other instance still converges."""
+    insts = _small_instances()
+    fs = [synthetic.fourier_field(it["shape"], 2 * np.pi, 6, 500 + i, nmodes=16) for i, it in enumerate(insts)]
+    fs[2][1, 1] = np.nan
+    B = Batch([dict(it, precision=PSD_FP64, tol=1e-10, max_iter=3000) for it in insts], workers=3)
+    us = [torch.zeros(it["shape"], dtype=torch.float64, device="cuda") for it in insts]
+    status, msg, infos = B.solve([dev(f) for f in fs], us, check=False)
+    assert status == 7 and "instance 2" in msg
+    for i, info in enumerate(infos):
+        if i == 2:
+            assert info["status"] == 7
+        else:
+            assert info["status"] == 0 and info["res_l2"] < 1e-10, i
