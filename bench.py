@@ -9,8 +9,18 @@ solved to ||r||_2 < 1e-10.  One step = one complete solve from u0.
 value = dof-iterations/s of the mixed-precision path (FP32 inner PSD with
 FP64 reductions and outer FP64 residual correction), counting inner FP32
 iterations and outer FP64 residual sweeps; the plain FP64 GPU path is timed
-beside it.  Inputs are resident in HBM when the timed region starts; every
-field (134 MB in FP64) is larger than L2, so no extra L2 flush is done.
+beside it.  Inputs are resident in HBM when the timed region starts.  No
+explicit L2 flush is done: one step (a whole solve) streams a working set of
+about 1.1 GB through every iteration, so nothing a step reads comes from L2
+left by the previous step; inside a solve the FP32 fields (67 MB each) can
+stay in the 129 MB L2 between consecutive kernels, which is a property of
+the iteration itself.
+
+Besides the headline line the bench times the other workloads of the
+benchmark family (2D 64^2 FP64; thin-film 1024^2 and 128^3, FP64 and
+mixed; the 96-instance batch; the 128^3 adjoint), a cuFFT R2C/C2R round trip
+beside the Hartley preconditioner at 256^3 (comparison only, never on the
+solver path), and the CPU oracle on one host core and on all host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -36,12 +46,17 @@ SAMPLE_N = 64          # grid of the CPU oracle sample (same workload family)
 SAMPLE_ITERS = 2       # PSD iterations per oracle sample
 
 
-def workload_config(n):
-    return {"workload": f"3D {n}^3 sixth-order PSD (SPFC-shaped: p=4, lambda=1, s=0.05, eps=0.1), "
-                        f"u0=mean(g), solve to ||r||_2<1e-10; mixed FP32/FP64 vs plain FP64",
+def workload_config(n, sample=None):
+    wl = (f"3D {n}^3 sixth-order PSD (SPFC-shaped: p=4, lambda=1, s=0.05, eps=0.1), "
+          f"u0=mean(g), solve to ||r||_2<1e-10; mixed FP32/FP64 vs plain FP64")
+    if sample:
+        wl = f"bounded sample of the {wl}: {sample}"
+    return {"workload": wl,
             "grid": [n, n, n], "order": 6, "tol": TOL,
-            "l2_flush": "none needed: every field (134 MB FP64 / 67 MB FP32) exceeds the 129 MB L2 "
-                        "or is streamed once per kernel"}
+            "l2_flush": "no explicit flush: a step (one whole solve) streams ~1.1 GB (5 FP64 fields of 134 MB "
+                        "and 7 FP32 fields of 67 MB) through every iteration, so no step starts from the "
+                        "previous step's L2 contents; within a solve the 67 MB FP32 fields can stay in the "
+                        "129 MB L2 between consecutive kernels"}
 
 
 # ------------------------------------------------------------------ helpers
@@ -180,28 +195,234 @@ def oracle_sample(iters=SAMPLE_ITERS, n=SAMPLE_N):
     return n ** 3 * iters / dt, dt
 
 
+def _oracle_worker(_):
+    return oracle_sample()
+
+
+def _oracle_warm(_):
+    from oracle import psd_oracle  # noqa: F401
+    from paper_1607_01475_gb300 import synthetic  # noqa: F401
+    return os.getpid()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample_all_cores(procs):
+    """The same oracle sample run as `procs` independent processes at once
+    (one per host core; a spawned pool, so no CUDA state is inherited):
+    whole-host throughput = procs samples / wall time of the batch."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_warm, range(procs))
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, range(procs))
+        wall = time.perf_counter() - t0
+    return procs * SAMPLE_N ** 3 * SAMPLE_ITERS / wall, wall, [r[1] for r in res]
+
+
+def cpu_baseline_record():
+    """Single-thread and all-cores oracle throughput on this host."""
+    v1, dt1 = oracle_sample()
+    cores = host_cores()
+    vall, wall, _ = oracle_sample_all_cores(cores)
+    sample = (f"{SAMPLE_ITERS} PSD iterations of the same sixth-order problem (same parameters and field "
+              f"recipe) on a {SAMPLE_N}^3 grid, numpy FP64; all cores: {cores} such samples as independent "
+              f"processes at once ({wall:.1f} s wall); one core: one sample ({dt1:.1f} s)")
+    return {"value": vall, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "cpu_model": cpu_model(), "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "seconds": dt1}}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        oracle_sample()
+    # each step: the oracle sample on every host core at once (independent
+    # processes of a spawned pool), so a step is ~SAMPLE_ITERS iterations of
+    # 64^3 per core, about 10-20 s of wall time
+    cores = host_cores()
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample_all_cores(cores)
     vals, times = [], []
     for _ in range(args.steps):
-        v, dt = oracle_sample()
+        v, wall, _ = oracle_sample_all_cores(cores)
         vals.append(v)
-        times.append(dt)
+        times.append(wall)
     value = statistics.median(vals)
     sample = (f"{SAMPLE_ITERS} PSD iterations of the same sixth-order problem (same parameters and "
-              f"field recipe) on a {SAMPLE_N}^3 grid per step; numpy FP64, single thread")
+              f"field recipe) on a {SAMPLE_N}^3 grid, numpy FP64, run as {cores} independent processes "
+              f"at once per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.n),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic",
+            "config": workload_config(args.n, sample=f"the CPU oracle, {SAMPLE_ITERS} PSD iterations on "
+                                                       f"{SAMPLE_N}^3 per process"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------- other workloads
+
+def _events_ms(torch, fn, reps, warm=2):
+    """Mean device milliseconds of fn() over reps calls (CUDA events on the
+    current stream, after warm calls)."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_workloads(args):
+    """Time-to-tolerance of the other workloads of the benchmark family, the
+    batch, the adjoint, and cuFFT beside the Hartley preconditioner."""
+    import numpy as np
+    import torch
+
+    from paper_1607_01475_gb300 import PSD_FP64, PSD_MIXED, Batch, Solver, synthetic
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+    out = {}
+
+    def solve_record(wl, precisions=(PSD_FP64, PSD_MIXED), reps=3):
+        shape = wl["shape"]
+        h = wl["L"] / shape[-1]
+        N = int(np.prod(shape))
+        f, g = dev(wl["f"]), (dev(wl["g"]) if wl.get("g") is not None else None)
+        u0 = dev(wl["u0"])
+        u = torch.empty_like(u0)
+        rec = {}
+        for prec in precisions:
+            S = Solver(wl["order"], shape, h, wl["p"], wl["s"], wl["eps"], wl.get("lam", 0.0), precision=prec,
+                       tol=TOL, max_iter=20000, max_outer=30)
+            infos = []
+
+            def one():
+                u.copy_(u0)
+                infos.append(S.solve(f, u, g))
+
+            ms = _events_ms(torch, one, reps)
+            info = infos[-1]
+            its = info["iters"] + info["outer_iters"]
+            name = "fp64" if prec == PSD_FP64 else "mixed"
+            rec[name] = {"time_to_tol_ms": ms, "iters": info["iters"], "outer_iters": info["outer_iters"],
+                         "res_l2": info["res_l2"], "dof_iter_per_s": N * its / (ms / 1000.0),
+                         "status": info["status"]}
+            S.close()
+        return rec
+
+    # 2D 64^2 fourth order, plain FP64
+    out["2d_64_fp64"] = dict(workload="2D 64^2 fourth-order, p=4, s=0.01, eps=0.1, f Fourier K=8, u0=0",
+                             **solve_record(synthetic.workload_small_2d(64), (PSD_FP64,), reps=10))
+    # thin-film shaped fourth order, FP64 and mixed
+    for shape, key in (((1024, 1024), "2d_1024_thinfilm"), ((128, 128, 128), "3d_128_thinfilm")):
+        out[key] = dict(workload=f"{'x'.join(map(str, shape))} fourth-order, p=4, s=0.1, eps=0.05, "
+                                 f"f = phi - s Delta phi (smoothed random phase field), u0=0",
+                        **solve_record(synthetic.workload_thin_film(shape)))
+        torch.cuda.empty_cache()
+
+    # 96-instance uneven batch (mixed and FP64), host wall time of one
+    # psd_batch_solve after a warm-up batch
+    wl = synthetic.workload_batch(96)
+    fs = [dev(w["f"]) for w in wl]
+    cells = sum(int(np.prod(w["shape"])) for w in wl)
+    brec = {"workload": "96 2D fourth-order instances, 64^2..1024^2, p in {3,4}, s in [1e-3,1e-1], "
+                        "eps in [0.02,0.2], each to its own tolerance", "cells": cells}
+    for prec, name in ((PSD_MIXED, "mixed"), (PSD_FP64, "fp64")):
+        insts = [dict(order=4, shape=w["shape"], h=w["L"] / w["shape"][-1], p=w["p"], s=w["s"], eps=w["eps"],
+                      precision=prec, tol=w["tol"], max_iter=20000, max_outer=30) for w in wl]
+        B = Batch(insts)
+        us = [torch.zeros(w["shape"], dtype=torch.float64, device="cuda") for w in wl]
+        B.solve(fs, us)
+        for u in us:
+            u.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = B.solve(fs, us)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) * 1000.0
+        dofit = sum(int(np.prod(w["shape"])) * (i["iters"] + i["outer_iters"]) for w, i in zip(wl, infos))
+        brec[name] = {"batch_wall_ms": wall, "dof_iter_per_s": dofit / (wall / 1000.0),
+                      "sum_instance_device_ms": sum(i["wall_ms"] for i in infos),
+                      "all_converged": all(i["status"] == 0 for i in infos)}
+        B.close()
+        del us
+    out["batch_96"] = brec
+    del fs
+    torch.cuda.empty_cache()
+
+    # adjoint at 128^3: forward FP64 solve, then dJ/df and dJ/ds
+    shape = (128, 128, 128)
+    wl = synthetic.workload_thin_film(shape)
+    h = wl["L"] / shape[-1]
+    ut = dev(synthetic.fourier_field(shape, wl["L"], 8, synthetic.seed_for(4, 0, 2)))
+    f = dev(wl["f"])
+    S = Solver(4, shape, h, wl["p"], wl["s"], wl["eps"], tol=TOL, max_iter=20000)
+    u = dev(wl["u0"])
+    S.solve(f, u)
+    gu = (u - ut) * h ** 3
+    gf = torch.empty_like(u)
+    infos = []
+    ms = _events_ms(torch, lambda: infos.append(S.adjoint(u, gu, gf)), 3, warm=1)
+    out["adjoint_128"] = {"workload": "3D 128^3 fourth-order thin-film solve, J = 1/2 h^3 sum (u - u_t)^2; "
+                                      "dJ/df and dJ/ds by preconditioned CG on the Hessian",
+                          "adjoint_ms": ms, "cg_iters": infos[-1][1]["iters"],
+                          "rel_res": infos[-1][1]["res_l2"]}
+    S.close()
+    del u, f, gu, gf, ut
+    torch.cuda.empty_cache()
+
+    # cuFFT (torch.fft) R2C + C2R round trip at 256^3 beside the Hartley
+    # preconditioner solve (which also divides by the symbol and forms the
+    # Parseval sums): a comparison only, never on the solver path
+    shape = (256, 256, 256)
+    h = 2 * np.pi / 256
+    cf = {"workload": "256^3 transform round trip", "note": "torch.fft (cuFFT) rfftn + irfftn vs the "
+          "library's preconditioner solve L_h d = r (Hartley passes + symbol division + Parseval sums)"}
+    for dt, name in ((torch.float32, "fp32"), (torch.float64, "fp64")):
+        x = torch.randn(shape, dtype=dt, device="cuda")
+        cf[f"cufft_r2c_c2r_ms_{name}"] = _events_ms(torch, lambda: torch.fft.irfftn(torch.fft.rfftn(x), s=shape),
+                                                    10)
+        S = Solver(6, shape, h, 4.0, 0.05, 0.1, 1.0, precision=PSD_MIXED if name == "fp32" else PSD_FP64)
+        y = torch.empty_like(x)
+        if name == "fp32":
+            cf[f"dht_precond_ms_{name}"] = _events_ms(torch, lambda: S.precond_solve_f32(x, y), 10)
+        else:
+            cf[f"dht_precond_ms_{name}"] = _events_ms(torch, lambda: S.precond_solve(x, y), 10)
+        S.close()
+        del x, y
+        torch.cuda.empty_cache()
+    out["cufft_comparison_256"] = cf
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -338,10 +559,14 @@ def run_gpu(args):
     # -------- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt = oracle_sample()
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{SAMPLE_ITERS} PSD iterations of the same sixth-order problem on a {SAMPLE_N}^3 "
-                         f"grid ({dt:.1f} s, numpy FP64, single thread)"}
+        cpu = cpu_baseline_record()
+
+    # -------- the other workloads of the benchmark family, cuFFT comparison
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        del mixed, fp64
+        torch.cuda.empty_cache()
+        extra = extra_workloads(args)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
@@ -359,7 +584,8 @@ def run_gpu(args):
             "kernel_ms_per_solve_mixed": {k: round(v[0], 3) for k, v in prof_all.items() if v[1]},
             "kernel_profile": "shares and ms from one untimed solve with every launch bracketed; roofline "
                               "from the timed solves, only the dominant class bracketed",
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": total_launches, "clocks": clk}
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": total_launches, "clocks": clk,
+            "other_workloads": extra}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -375,6 +601,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads and the cuFFT comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -230,6 +230,17 @@ psd_status psd_spfc_steps(psd_handle h, double* u, double gamma1, int nsteps,
 psd_status psd_residual_fixed(psd_handle h, const double* u, const double* f,
                               double* r, int* scale);
 
+/* The float-float transform passes of the mixed sixth-order solver's outer
+ * loop, for tests: theta += H[T_h x], with H the unnormalised separable
+ * discrete Hartley transform (kernel prod_a cas(2 pi j_a k_a / n_a), which
+ * diagonalises the symbols of Sec. 5.1 like the DFT of Sec. 6 does) and
+ * T_h = -Delta_h^{-1} on the mean-zero space (Sec. 5.1; the zero mode
+ * gives 0), computed in double-word arithmetic (about 48 significant bits)
+ * on FP64 storage.  x, theta: device, N doubles each, must not alias; the
+ * handle's direction buffer is used as scratch.  Synchronises the stream.
+ * Errors: PSD_ERR_INVALID for null pointers.                               */
+psd_status psd_theta_ff(psd_handle h, const double* x, double* theta);
+
 /* Kernel classes reported by psd_profile_read (index = class).            */
 enum {
   PSD_PROF_RESIDUAL_FP64 = 0, PSD_PROF_RESIDUAL_FP32 = 1,
@@ -274,8 +285,8 @@ const char* psd_profile_class_name(int k);
  * allocation, and fixed-budget deployments.  The kernel's scratch (block
  * partial sums and the reduction control block) is a file-scope __device__
  * array of about 33 KB that every GPU loading the library keeps until exit.
- * params: order must be 4; its stream is used; tol, max_iter, max_outer and
- * precision are ignored.  u, f, r: device arrays as for psd_residual (r is
+ * params: order must be 4 and, as for psd_create, p <= 6 in 3D; its stream
+ * is used; tol, max_iter, max_outer and precision are ignored.  u, f, r: device arrays as for psd_residual (r is
  * required); res_l2 / res_linf: host pointers or NULL.  Synchronises the
  * stream.  Returns PSD_ERR_INVALID for a bad size or parameter, including
  * grids whose residual launch needs more than 2048 blocks (none of the

@@ -94,6 +94,7 @@ def load_library(build_if_missing=True):
     lib.psd_thinfilm_adjoint.argtypes = [H, D, ctypes.c_int, D, D, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                          ctypes.c_double, ctypes.c_int, ctypes.POINTER(PSDInfo)]
     lib.psd_precond_solve_f32.argtypes = [H, F, F]
+    lib.psd_theta_ff.argtypes = [H, D, D]
     lib.psd_energy.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.psd_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
     lib.psd_profile.argtypes = [H, ctypes.c_int]
@@ -116,7 +117,7 @@ def load_library(build_if_missing=True):
     lib.psd_status_string.argtypes = [ctypes.c_int]
     lib.psd_status_string.restype = ctypes.c_char_p
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
-                 "psd_set_history", "psd_residual_f32", "psd_residual_fixed", "psd_thinfilm_steps", "psd_spfc_steps", "psd_thinfilm_adjoint", "psd_last_error",
+                 "psd_set_history", "psd_residual_f32", "psd_residual_fixed", "psd_theta_ff", "psd_thinfilm_steps", "psd_spfc_steps", "psd_thinfilm_adjoint", "psd_last_error",
                  "psd_profile",
                  "psd_profile_read", "psd_profile_classes", "psd_residual_noalloc", "psd_noalloc_last_error",
                  "psd_precond_solve_f32", "psd_energy",
@@ -275,6 +276,11 @@ def psd_residual_fixed(handle, u, f, r):
     return scale.value
 
 
+def psd_theta_ff(handle, x, theta):
+    """theta += H[T_h x] by the float-float transform passes (see include/psd.h)."""
+    _check(load_library().psd_theta_ff(handle, _ptr(x), _ptr(theta)), handle)
+
+
 def psd_residual_noalloc(shape, h, p, s, eps, u, f, r, stream=None):
     """Fourth-order residual and norms without a handle or any device
     allocation (see include/psd.h).  Returns (||r||_2, max|r|)."""
@@ -388,6 +394,9 @@ class Solver:
 
     def residual_fixed(self, u, f, r):
         return psd_residual_fixed(self.handle, u, f, r)
+
+    def theta_ff(self, x, theta):
+        psd_theta_ff(self.handle, x, theta)
 
     def thinfilm_steps(self, u, nsteps):
         return psd_thinfilm_steps(self.handle, u, nsteps)

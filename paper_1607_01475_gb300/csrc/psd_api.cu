@@ -1005,6 +1005,20 @@ psd_status psd_residual_fixed(psd_handle c, const double* u, const double* f, do
   return PSD_OK;
 }
 
+psd_status psd_theta_ff(psd_handle c, const double* x, double* theta) {
+  if (!c) return PSD_ERR_INVALID;
+  if (!x || !theta) return fail(c, PSD_ERR_INVALID, "x and theta are required");
+  TRY(ensure_fp64(c));
+  const KParams& kp = c->kp;
+  const int nrows = kp.ny * kp.nz;
+  psd::ff* w = reinterpret_cast<psd::ff*>(c->D);
+  { ProfScope p_(c, PSD_PROF_DHT_ROWS_FF); CK(psd::launch_dht_rows_ff(x, w, kp.nx, nrows, c->tbff, c->st)); }
+  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(w, kp, 1, c->tbff, c->st)); }
+  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(w, theta, nullptr, kp, nullptr, c->partials, c->tbff, c->st)); }
+  CK(cudaStreamSynchronize(c->st));
+  return PSD_OK;
+}
+
 psd_status psd_precond_solve(psd_handle c, const double* r, double* d) {
   if (!c) return PSD_ERR_INVALID;
   if (!r || !d) return fail(c, PSD_ERR_INVALID, "r and d are required");

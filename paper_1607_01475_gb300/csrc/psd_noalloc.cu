@@ -64,6 +64,7 @@ extern "C" psd_status psd_residual_noalloc(const psd_params* prm, const double* 
   if (!(prm->h > 0) || !std::isfinite(prm->h) || !(prm->p >= 2) || !std::isfinite(prm->p) ||
       !(prm->s > 0) || !std::isfinite(prm->s) || !(prm->eps > 0) || !std::isfinite(prm->eps))
     return err(PSD_ERR_INVALID, "h, s, eps must be positive and p >= 2");
+  if (prm->dim == 3 && prm->p > 6) return err(PSD_ERR_INVALID, "3D requires p <= 6");
   psd::KParams kp{};
   kp.nx = prm->n[0];
   kp.ny = prm->n[1];

@@ -280,18 +280,25 @@ def test_second_order_consistency(oracle, p):
     s, eps = 0.1, 0.3
     uf, Nf = _continuous_N4(p, s, eps)
     P = None
-    errs = []
-    for n in (32, 64, 128, 256):
+    errs, hs = [], []
+    for n in (32, 64, 128, 256, 512):
         h = 2 * np.pi / n
         c = (np.arange(n) + 0.5) * h
         Y, X = np.meshgrid(c, c, indexing="ij")
         P = oracle.Problem(4, h, p, s, eps)
         e = oracle.N4(uf(X, Y), P) - Nf(X, Y)
         errs.append(np.max(np.abs(e)))
-    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-    # asymptotically second order: the finest rate is 2 within 0.05 and the
-    # rates approach it from the pre-asymptotic side
-    assert 1.95 < rates[-1] < 2.05 and np.all(rates > 1.7) and np.all(np.diff(rates) > -0.02), rates
+        hs.append(h)
+    errs, hs = np.array(errs), np.array(hs)
+    rates = np.log2(errs[:-1] / errs[1:])
+    # Second order, reached from the pre-asymptotic side: at p = 6 the flux
+    # |grad u|^4 grad u carries a large h^4 term, so the coarse rates are
+    # 1.82, 1.93, 1.99 before 2.00.  The finest rate must be 2 within 0.01,
+    # every rate above 1.7, and the error constant e / h^2 settled to 1%
+    # between the two finest grids (a first-order or O(h^3) error fails both).
+    const = errs / hs ** 2
+    assert 1.99 < rates[-1] < 2.01 and np.all(rates > 1.7), rates
+    assert abs(const[-1] - const[-2]) < 0.01 * const[-1], const
 
 
 # ------------------------------------------- symmetries

@@ -77,3 +77,16 @@ def test_noalloc_rejects_sixth_order():
     x = torch.zeros((64, 64), dtype=torch.float64, device="cuda")
     ptr = ctypes.c_void_p(x.data_ptr())
     assert lib.psd_residual_noalloc(ctypes.byref(prm), ptr, ptr, ptr, None, None) == 1
+
+
+def test_noalloc_rejects_3d_p_above_6():
+    """The same parameter rule as psd_create: p <= 6 in 3D (Sec. 3.1)."""
+    lib = _lib.load_library()
+    prm = _lib.PSDParams(order=4, dim=3, n=(ctypes.c_int * 3)(16, 16, 16), h=0.1, p=7.0, s=0.1, eps=0.1,
+                         lam=0.0, precision=0, tol=0.0, max_iter=0, max_outer=0, stream=None)
+    x = torch.zeros((16, 16, 16), dtype=torch.float64, device="cuda")
+    ptr = ctypes.c_void_p(x.data_ptr())
+    assert lib.psd_residual_noalloc(ctypes.byref(prm), ptr, ptr, ptr, None, None) == 1
+    buf = ctypes.create_string_buffer(256)
+    lib.psd_noalloc_last_error(buf, len(buf))
+    assert b"p <= 6" in buf.value
