@@ -350,6 +350,25 @@ def extra_workloads(args):
                         **solve_record(synthetic.workload_thin_film(shape)))
         torch.cuda.empty_cache()
 
+    # thin-film convex-splitting time loop (Sec. 6.1) at 512^2 with the
+    # initial data of Eq. "init1", s = 0.1 h^2, eps = 0.1: ms per time step
+    # (device time of 50 steps after 5), p = 4 and 6, FP64 and mixed
+    tl = {"workload": "thin-film time loop, 512^2 on (0,3.2)^2, Eq. init1 data, s=0.1h^2, eps=0.1, "
+                      "each step solved to ||r||_2<1e-10 from u^n"}
+    u0, h = synthetic.thin_film_init1(512)
+    for p_ in (4.0, 6.0):
+        for prec, name in ((PSD_FP64, "fp64"), (PSD_MIXED, "mixed")):
+            S = Solver(4, (512, 512), h, p_, 0.1 * h * h, 0.1, precision=prec, tol=TOL, max_iter=20000,
+                       max_outer=30)
+            u = dev(u0)
+            S.thinfilm_steps(u, 5)
+            info = S.thinfilm_steps(u, 50)
+            tl[f"p{int(p_)}_{name}"] = {"ms_per_step": info["wall_ms"] / 50,
+                                        "iters_per_step": info["iters"] / 50,
+                                        "outer_per_step": info["outer_iters"] / 50}
+            S.close()
+    out["thinfilm_512_steps"] = tl
+
     # 96-instance uneven batch (mixed and FP64), host wall time of one
     # psd_batch_solve after a warm-up batch
     wl = synthetic.workload_batch(96)

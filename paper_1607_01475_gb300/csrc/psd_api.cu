@@ -415,7 +415,7 @@ psd_status precond_passes(psd_context* c, T* W, T* D, Ctrl* ctrl, T* xi, T* dspe
 
 template <typename T>
 psd_status linesearch(psd_context* c, const T* u, const T* ubase, const T* D, Ctrl* ctrl) {
-  const int passes = (c->pk == psd::PK_4) ? 1 : kLsPassesGen;
+  const int passes = (c->pk == psd::PK_GEN) ? kLsPassesGen : 1;
   for (int i = 0; i < passes; ++i) {
     ProfScope p_(c, cls_of<T>(PSD_PROF_LINESEARCH_FP64));
     CK(psd::launch_linesearch<T>(u, ubase, D, c->pk, c->kp, ctrl, c->partials, c->st));
@@ -820,7 +820,7 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
   c->N = (size_t)kp.nx * kp.ny * kp.nz;
   kp.inv_ntot = 1.0 / (double)c->N;
   psd::finish_kparams(kp);
-  c->pk = (params->p == 4.0) ? psd::PK_4 : psd::PK_GEN;
+  c->pk = (params->p == 4.0) ? psd::PK_4 : (params->p == 6.0) ? psd::PK_6 : psd::PK_GEN;
   static const bool attrs = (psd::init_dht_attributes(), true);  // once, thread-safe
   (void)attrs;
 

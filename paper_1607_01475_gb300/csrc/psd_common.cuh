@@ -9,8 +9,9 @@
 
 namespace psd {
 
-// Kinds of the vertex factor |g|^{p-2}: specialised p = 4 and a general p.
-enum PKind { PK_GEN = 0, PK_4 = 4 };
+// Kinds of the vertex factor |g|^{p-2}: specialised p = 4 (|g|^2) and
+// p = 6 (|g|^4 = (|g|^2)^2), and a general p (pow).
+enum PKind { PK_GEN = 0, PK_4 = 4, PK_6 = 6 };
 
 // Slots of the "last block" counters in the control block.
 enum CounterSlot { CS_RES = 0, CS_MID = 1, CS_LS = 2, CS_MISC = 3, CS_COUNT = 8 };
@@ -31,7 +32,9 @@ struct Ctrl {
   double dd;       // (d, d)_2
   double lapdd;    // (Delta_h d, Delta_h d)_2
   double tdd;      // (T_h d, d)_2 (order 6)
-  // line-search sums (weighted by h^d): p = 4 polynomial coefficients
+  // line search: the first three polynomial coefficients of q (p = 4, 6;
+  // weighted by h^d and s), or the general-p Newton state (c1, c2 = bracket,
+  // c3 = converged flag)
   double c1, c2, c3;
   // inner (mixed-precision) stop on the preconditioned residual norm
   // (r, L_h^{-1} r)^{1/2} = ||d||_L (Eq. "RRT-1"): done when it drops below

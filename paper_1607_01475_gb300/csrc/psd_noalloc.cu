@@ -113,7 +113,7 @@ extern "C" psd_status psd_residual_noalloc(const psd_params* prm, const double* 
   cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(psd::Ctrl), st);
   if (e != cudaSuccess) return err(PSD_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   psd::ResArgs<double> a{u, nullptr, nullptr, f, nullptr, r, 1, 0};
-  const int pk = (prm->p == 4.0) ? psd::PK_4 : psd::PK_GEN;
+  const int pk = (prm->p == 4.0) ? psd::PK_4 : (prm->p == 6.0) ? psd::PK_6 : psd::PK_GEN;
   e = psd::launch_residual<double>(a, psd::RM_PLAIN, pk, kp, ctrl, partials, st);
   if (e != cudaSuccess) return err(PSD_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString(e));
   double norms[2];

@@ -391,17 +391,17 @@ __global__ void __launch_bounds__(256, 3)
     k_ls3d_col(const T* __restrict__ u, const T* __restrict__ ubase, const T* __restrict__ d, KParams kp,
                Ctrl* ctrl, double* partials) {
   if (ctrl->done) return;
-  if (PK != PK_4 && ctrl->c3 != 0.0) return;  // Newton already converged
+  if (!ls_closed_form<PK>() && ctrl->c3 != 0.0) return;  // Newton already converged
   constexpr int TX = 32, TY = 8;
   constexpr int SX = TX + 1, SY = TY + 1, SN = SX * SY;  // cells x0..x0+TX, y0..y0+TY
   __shared__ T sPu[2][SY][SX], sMu[2][SY][SX], sPd[2][SY][SX], sMd[2][SY][SX];
-  __shared__ T sred[32 * 3];
+  __shared__ T sred[32 * ls_nsums<PK>()];
   __shared__ int sflag;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
   const size_t plane = (size_t)nx * ny;
   const T beta = kconst<T>(kp).beta, pm2 = kconst<T>(kp).pm2;
-  const T trial = (PK == PK_4) ? T(0) : (T)ctrl->alpha;
+  const T trial = ls_closed_form<PK>() ? T(0) : (T)ctrl->alpha;
   // one wave of CTAs, each marching an equal share of the column-planes (as
   // the residual column kernel)
   const int gx = nx / TX;
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(256, 3)
     g[1] = (P[ty + 1][tx] - P[ty][tx]) + (P[ty + 1][tx + 1] - P[ty][tx + 1]);
     g[2] = (M[ty][tx] + M[ty][tx + 1]) + (M[ty + 1][tx] + M[ty + 1][tx + 1]);
   };
-  T acc[3] = {T(0), T(0), T(0)};
+  T acc[ls_nsums<PK>()] = {};
   for (int w = (int)((long long)wtot * blockIdx.x / gridDim.x); w < wend;) {
     const int col = w / nz, z0 = w - col * nz;
     const int zc = min(nz - z0, wend - w);
@@ -475,16 +475,7 @@ __global__ void __launch_bounds__(256, 3)
     }
     __syncthreads();  // the next segment writes the shared buffers again
   }
-  T v[3] = {acc[0], acc[1], acc[2]};
-  block_reduce<T, 3, false>(v, sred);
-  if (publish_and_check_last<T>(v, 3, reinterpret_cast<T*>(partials), &ctrl->counter[CS_LS], &sflag)) {
-    T tt[3];
-    gather_partials<T, 3, false>(tt, reinterpret_cast<const T*>(partials), sred);
-    if (tid == 0) {
-      const double tot[3] = {(double)tt[0], (double)tt[1], (double)tt[2]};
-      linesearch_epilogue<PK>(ctrl, kp, tot);
-    }
-  }
+  ls_finish<T, PK>(acc, sred, partials, ctrl, kp, &sflag);
 }
 
 }  // namespace

@@ -149,6 +149,18 @@ def workload_spfc(shape=(256, 256, 256)):
                 lam=1.0, f=f, g=g, u0=u0)
 
 
+def thin_film_init1(n, L=3.2):
+    """The analytic initial data of the thin-film convergence test (Sec. 6.1.1,
+    Eq. "init1") on (0, L)^2 at cell centres:
+    0.1 sin^2(2 pi x / L) sin(4 pi (y - 1.4) / L) - 0.1 cos(2 pi (x - 2) / L) sin(2 pi y / L).
+    Returns (u0, h)."""
+    h = L / n
+    x = (np.arange(n) + 0.5) * h
+    y = x[:, None]
+    return (0.1 * np.sin(2 * np.pi * x / L) ** 2 * np.sin(4 * np.pi * (y - 1.4) / L)
+            - 0.1 * np.cos(2 * np.pi * (x - 2.0) / L) * np.sin(2 * np.pi * y / L)), h
+
+
 def workload_batch(count=96, max_exp=5):
     """Uneven 2D fourth-order instances on (0, 2pi)^2: n = 2^(6 + floor(max_exp U))
     (64..1024 for max_exp = 5), s = 10^(-3 + 2U), eps uniform in [0.02, 0.2],

@@ -53,7 +53,7 @@ def _problem(oracle, order, shape, p, s=0.1, eps=0.2, lam=0.7):
 # ---------------------------------------------------------------- residual
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("order,p", [(4, 4.0), (4, 3.0), (6, 4.0), (4, 6.0)])
+@pytest.mark.parametrize("order,p", [(4, 4.0), (4, 3.0), (6, 4.0), (4, 6.0), (6, 6.0), (4, 5.0)])
 def test_residual_parity(oracle, shape, order, p):
     P, h = _problem(oracle, order, shape, p)
     u = rng.standard_normal(shape) * 0.3
@@ -142,7 +142,7 @@ RB_SHAPE_SHORT = (32, 512, 512)
 
 
 @pytest.mark.parametrize("shape", [RB_SHAPE, RB_SHAPE_SHORT])
-@pytest.mark.parametrize("p", [4.0, 3.0])
+@pytest.mark.parametrize("p", [4.0, 3.0, 6.0])
 def test_residual_f32_register_blocked(oracle, p, shape):
     """The register-blocked FP32 residual kernel against the FP64 oracle on
     a grid that selects it.  Rough fields (as in the FP64 parity test): a
@@ -162,7 +162,7 @@ def test_residual_f32_register_blocked(oracle, p, shape):
 
 
 @pytest.mark.parametrize("shape", [RB_SHAPE, RB_SHAPE_SHORT])
-@pytest.mark.parametrize("p", [4.0, 3.0])
+@pytest.mark.parametrize("p", [4.0, 3.0, 6.0])
 def test_mixed_solve_register_blocked(p, shape):
     """Mixed precision on a grid that selects the register-blocked FP32
     residual and line-search kernels (inner correction form, p = 4 and a
@@ -221,7 +221,7 @@ def test_precond_parity(oracle, shape, order):
 # ------------------------------------------------------------ PSD iterates
 
 @pytest.mark.parametrize("shape", [(64, 64), (16, 16, 16), (8, 16, 32), (8, 8), (8, 8, 8), (32, 64, 16)])
-@pytest.mark.parametrize("order,p", [(4, 4.0), (6, 4.0), (4, 3.0), (4, 6.0)])
+@pytest.mark.parametrize("order,p", [(4, 4.0), (6, 4.0), (4, 3.0), (4, 6.0), (6, 6.0), (4, 5.0)])
 def test_iterates_parity(oracle, shape, order, p):
     """u^k and alpha_k for k = 1..5 from the same u^0."""
     P, h = _problem(oracle, order, shape, p, s=0.05, eps=0.15, lam=1.0)
@@ -264,7 +264,7 @@ def test_converged_parity_fp64(oracle, shape, order, p):
 
 
 @pytest.mark.parametrize("shape", [(64, 64), (16, 16, 16), (8, 32, 16), (8, 8)])
-@pytest.mark.parametrize("order,p", [(4, 4.0), (6, 4.0), (4, 3.0)])
+@pytest.mark.parametrize("order,p", [(4, 4.0), (6, 4.0), (4, 3.0), (4, 6.0), (6, 6.0)])
 def test_mixed_precision_parity(oracle, shape, order, p):
     """FP32 inner PSD + outer FP64 residual correction reaches the FP64
     solution to 1e-9 relative."""

@@ -28,12 +28,7 @@ def rel(a, b):
 
 
 def _init1(n):
-    L = 3.2
-    h = L / n
-    x = (np.arange(n) + 0.5) * h
-    y = x[:, None]
-    return (0.1 * np.sin(2 * np.pi * x / L) ** 2 * np.sin(4 * np.pi * (y - 1.4) / L)
-            - 0.1 * np.cos(2 * np.pi * (x - 2.0) / L) * np.sin(2 * np.pi * y / L)), h
+    return synthetic.thin_film_init1(n)
 
 
 @pytest.mark.parametrize("n,p,nsteps", [(16, 4.0, 20), (32, 4.0, 40), (32, 6.0, 20)])
