@@ -87,7 +87,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -405,19 +405,23 @@ def extra_workloads(args):
     h = wl["L"] / shape[-1]
     ut = dev(synthetic.fourier_field(shape, wl["L"], 8, synthetic.seed_for(4, 0, 2)))
     f = dev(wl["f"])
-    S = Solver(4, shape, h, wl["p"], wl["s"], wl["eps"], tol=TOL, max_iter=20000)
-    u = dev(wl["u0"])
-    S.solve(f, u)
-    gu = (u - ut) * h ** 3
-    gf = torch.empty_like(u)
-    infos = []
-    ms = _events_ms(torch, lambda: infos.append(S.adjoint(u, gu, gf)), 3, warm=1)
-    out["adjoint_128"] = {"workload": "3D 128^3 fourth-order thin-film solve, J = 1/2 h^3 sum (u - u_t)^2; "
-                                      "dJ/df and dJ/ds by preconditioned CG on the Hessian",
-                          "adjoint_ms": ms, "cg_iters": infos[-1][1]["iters"],
-                          "rel_res": infos[-1][1]["res_l2"]}
-    S.close()
-    del u, f, gu, gf, ut
+    adj = {"workload": "3D 128^3 fourth-order thin-film solve, J = 1/2 h^3 sum (u - u_t)^2; dJ/df and dJ/ds "
+                       "by device-resident preconditioned CG on the Hessian to 1e-12 relative (mixed: FP32 inner "
+                       "CG, FP64 outer residual correction)"}
+    for prec, name in ((PSD_FP64, "fp64"), (PSD_MIXED, "mixed")):
+        S = Solver(4, shape, h, wl["p"], wl["s"], wl["eps"], precision=prec, tol=TOL, max_iter=20000, max_outer=30)
+        u = dev(wl["u0"])
+        S.solve(f, u)
+        gu = (u - ut) * h ** 3
+        gf = torch.empty_like(u)
+        infos = []
+        ms = _events_ms(torch, lambda: infos.append(S.adjoint(u, gu, gf, tol_rel=1e-12)), 3, warm=1)
+        adj[name] = {"adjoint_ms": ms, "cg_iters": infos[-1][1]["iters"], "outer": infos[-1][1]["outer_iters"],
+                     "rel_res": infos[-1][1]["res_l2"]}
+        S.close()
+        del u, gu, gf
+    out["adjoint_128"] = adj
+    del f, ut
     torch.cuda.empty_cache()
 
     # cuFFT (torch.fft) R2C + C2R round trip at 256^3 beside the Hartley

@@ -149,15 +149,22 @@ psd_status psd_hvp(psd_handle h, const double* u, const double* v, double* y,
 
 /* Gradient of a loss J(u) of the converged solution u of N_h[u] = f with
  * respect to f and s (order 4).  Not in the paper: by the implicit function
- * theorem, H lambda = grad_u (H symmetric, solved by conjugate gradients
- * preconditioned with the FFT solve of L_h), grad_f = lambda and
- * grad_s = -sum_i lambda_i (dN_h/ds)_i, dN_h/ds = -grad_h^v.(|Du|^{p-2}Du)
- * + eps^2 Delta_h^2 u.  u, grad_u: device arrays (grad_u = dJ/du entrywise);
- * grad_f: device output (may alias grad_u); grad_s: host double (may be
- * NULL).  The solve stops when ||r||_2 <= tol_rel ||grad_u||_2 (tol_rel <= 0
- * selects 1e-12) or after max_iter iterations (PSD_ERR_NOCONV).  info (may
- * be NULL): iters = CG iterations, res_l2 = final relative residual.  Uses
- * the handle's workspace; synchronises the stream.                        */
+ * theorem, H lambda = grad_u (H = dN_h/du, the second variation of Sec. 5.3,
+ * symmetric positive definite, solved by conjugate gradients preconditioned
+ * with the FFT solve of L_h), grad_f = lambda and grad_s = -sum_i lambda_i
+ * (dN_h/ds)_i, dN_h/ds = -grad_h^v.(|Du|^{p-2}Du) + eps^2 Delta_h^2 u.
+ * The CG loop is device resident (step lengths and the stop flag in device
+ * memory, chunks of iterations replayed from a CUDA graph).  On a PSD_FP64
+ * handle it runs in FP64; on a PSD_MIXED handle the FP64 residual
+ * R = grad_u - H lambda is corrected by FP32 CG solves of H delta = R (H at
+ * the FP32 copy of u) to inner_eta ||R|| (default 1e-4).
+ * u, grad_u: device arrays (grad_u = dJ/du entrywise); grad_f: device output
+ * (may alias grad_u); grad_s: host double (may be NULL).  The solve stops
+ * when ||grad_u - H lambda||_2 <= tol_rel ||grad_u||_2 (tol_rel <= 0 selects
+ * 1e-12) or after max_iter CG iterations (PSD_ERR_NOCONV).  info (may be
+ * NULL): iters = CG iterations (mixed: FP32 inner iterations), outer_iters =
+ * FP64 residual evaluations (mixed), res_l2 = final relative residual.
+ * Uses the handle's workspace; synchronises the stream.                   */
 psd_status psd_adjoint(psd_handle h, const double* u, const double* grad_u,
                        double* grad_f, double* grad_s, double tol_rel,
                        int max_iter, psd_info* info);
@@ -241,6 +248,17 @@ psd_status psd_residual_fixed(psd_handle h, const double* u, const double* f,
  * Errors: PSD_ERR_INVALID for null pointers.                               */
 psd_status psd_theta_ff(psd_handle h, const double* x, double* theta);
 
+/* Autotuner (not in the paper): choose the tile widths -- line pairs per
+ * thread block -- of the FP32 row, strided-axis and middle transform passes
+ * of a PSD_MIXED handle by timing each candidate on the handle's own buffers
+ * over a few preconditioner solves, and use the fastest from then on.  The
+ * choice is cached for the process by grid shape and order, so tuning a
+ * second handle of the same shape costs nothing; psd_batch_create tunes
+ * every mixed instance.  caps (host, 3 ints, may be NULL) receives the
+ * chosen caps (0 = the widest tile, 256 threads).  A no-op for PSD_FP64
+ * handles.  Synchronises the handle's stream.                              */
+psd_status psd_autotune(psd_handle h, int* caps);
+
 /* Kernel classes reported by psd_profile_read (index = class).            */
 enum {
   PSD_PROF_RESIDUAL_FP64 = 0, PSD_PROF_RESIDUAL_FP32 = 1,
@@ -303,16 +321,23 @@ psd_status psd_residual_noalloc(const psd_params* params, const double* u,
 psd_status psd_noalloc_last_error(char* buf, size_t len);
 
 /* ---- Batches of independent instances (many uneven problem sizes). ----
- * psd_batch_create makes one solver per parameter set (each with its own
- * non-blocking stream; the stream fields of per_instance are ignored) and a
- * pool of `workers` host threads (<= 0: min(count, 16)).  psd_batch_solve
- * solves every instance i from the initial guess in u[i] (device arrays of
- * instance i's size; g[i] for order-6 instances, g may be NULL when none is
- * order 6) concurrently: the instances' kernels overlap on the GPU.  It
- * synchronises the device before starting and returns when all instances
- * are done; infos (host, count entries, may be NULL) receives per-instance
- * statistics; the status is PSD_OK or the first failing instance's status
- * (psd_batch_last_error names it).                                        */
+ * Not in the paper.  psd_batch_create makes one solver per parameter set
+ * (each with its own non-blocking stream; the stream fields of per_instance
+ * are ignored).  psd_batch_solve solves every instance i from the initial
+ * guess in u[i] (device arrays of instance i's size; g[i] for order-6
+ * instances, g may be NULL when none is order 6) concurrently, from ONE CUDA
+ * graph launch: each instance's solve -- its loops are conditional WHILE
+ * nodes driven by its device-resident stop flags -- is a branch of a single
+ * graph captured on the first call (and again when a pointer changes), so
+ * the instances' kernels overlap on the GPU with no host round trip.  When
+ * a capture is not possible (kernel tracing on, or a capture failure) the
+ * solves run from a pool of `workers` host threads (<= 0: min(count, 16)).
+ * It synchronises the device before starting and returns when all
+ * instances are done; infos (host, count entries, may be NULL) receives
+ * per-instance statistics (wall_ms: the instance's own span inside the
+ * graph); the status is PSD_OK or the first failing instance's status
+ * (psd_batch_last_error names it).  A failing instance does not stop the
+ * others.                                                                 */
 typedef struct psd_batch_ctx* psd_batch;
 psd_status psd_batch_create(const psd_params* per_instance, int count,
                             int workers, psd_batch* out);
@@ -321,6 +346,9 @@ psd_status psd_batch_solve(psd_batch b, const double* const* f,
                            psd_info* infos);
 psd_status psd_batch_destroy(psd_batch b);
 psd_status psd_batch_last_error(psd_batch b, char* buf, size_t len);
+/* How the last psd_batch_solve ran: 1 = one graph launch, 2 = host threads
+ * (0 = none yet or b NULL).                                                */
+int psd_batch_mode(psd_batch b);
 
 /* Text of the last error on this handle (or of the last psd_create failure
  * when h is NULL), copied into buf (always NUL-terminated).                */

@@ -95,6 +95,7 @@ def load_library(build_if_missing=True):
                                          ctypes.c_double, ctypes.c_int, ctypes.POINTER(PSDInfo)]
     lib.psd_precond_solve_f32.argtypes = [H, F, F]
     lib.psd_theta_ff.argtypes = [H, D, D]
+    lib.psd_autotune.argtypes = [H, P]
     lib.psd_energy.argtypes = [H, D, D, D, ctypes.POINTER(ctypes.c_double)]
     lib.psd_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
     lib.psd_profile.argtypes = [H, ctypes.c_int]
@@ -111,13 +112,15 @@ def load_library(build_if_missing=True):
                                     ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PSDInfo)]
     lib.psd_batch_destroy.argtypes = [H]
     lib.psd_batch_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
+    lib.psd_batch_mode.argtypes = [H]
+    lib.psd_batch_mode.restype = ctypes.c_int
     lib.psd_residual_noalloc.argtypes = [ctypes.POINTER(PSDParams), D, D, D, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     lib.psd_noalloc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     lib.psd_status_string.argtypes = [ctypes.c_int]
     lib.psd_status_string.restype = ctypes.c_char_p
     for name in ("psd_create", "psd_destroy", "psd_residual", "psd_precond_solve", "psd_solve",
-                 "psd_set_history", "psd_residual_f32", "psd_residual_fixed", "psd_theta_ff", "psd_thinfilm_steps", "psd_spfc_steps", "psd_thinfilm_adjoint", "psd_last_error",
+                 "psd_set_history", "psd_residual_f32", "psd_residual_fixed", "psd_theta_ff", "psd_autotune", "psd_thinfilm_steps", "psd_spfc_steps", "psd_thinfilm_adjoint", "psd_last_error",
                  "psd_profile",
                  "psd_profile_read", "psd_profile_classes", "psd_residual_noalloc", "psd_noalloc_last_error",
                  "psd_precond_solve_f32", "psd_energy",
@@ -347,6 +350,10 @@ class Batch:
             raise PSDError(st, msg)
         return [i.as_dict() for i in infos]
 
+    def mode(self):
+        """1: the last solve ran from one graph launch; 2: from host threads."""
+        return load_library().psd_batch_mode(self.handle)
+
     def close(self):
         if self.handle:
             load_library().psd_batch_destroy(self.handle)
@@ -394,6 +401,13 @@ class Solver:
 
     def residual_fixed(self, u, f, r):
         return psd_residual_fixed(self.handle, u, f, r)
+
+    def autotune(self):
+        """Tile widths of the FP32 transform passes (see include/psd.h);
+        returns the three chosen caps."""
+        caps = (ctypes.c_int * 3)()
+        _check(load_library().psd_autotune(self.handle, caps), self.handle)
+        return list(caps)
 
     def theta_ff(self, x, theta):
         psd_theta_ff(self.handle, x, theta)

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpsd.so")
 
-SOURCES = ["psd_api.cu", "psd_batch.cu", "psd_noalloc.cu", "k_stencil.cu", "k_res_p4.cu", "k_res_p6.cu",
+SOURCES = ["psd_api.cu", "psd_batch.cu", "psd_noalloc.cu", "k_loop.cu", "k_stencil.cu", "k_res_p4.cu", "k_res_p6.cu",
            "k_res_pgen.cu", "k_dht_f32.cu", "k_dht_f64.cu", "k_dht_ff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -7,6 +7,7 @@
 // k_dht_ff.cu, each of which instantiates one arithmetic type.
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 
 #include "fft_line.cuh"
@@ -192,9 +193,10 @@ __global__ void __launch_bounds__(kThreads)
     k_dht_last_ff(const ff* data, double* theta, float* out32, size_t line_stride, size_t outer_stride,
                   KParams kp, Ctrl* ctrl, double* partials, const ff* __restrict__ twc,
                   const ff* __restrict__ tws, const ff* __restrict__ symx, const ff* __restrict__ symo,
-                  const ff* __restrict__ syml, double* dc) {
+                  const ff* __restrict__ syml, double* dc, const int* skip) {
   using T = ff;
   using F = LineFFT<T, N, RM>;
+  if (skip != nullptr && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ float sred[32];
@@ -270,132 +272,15 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// ------------------------------------------------------------- middle pass
-template <typename T, int N, int ORDER, int RM>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 && ORDER == 4 ? 3 : 2)
-    k_mid(T* data, size_t line_stride, size_t outer_stride, KParams kp, Ctrl* ctrl, double* partials,
-          T* xi, T* dspec, const T* __restrict__ symx, const T* __restrict__ symo,
-          const T* __restrict__ syml, const T* __restrict__ twc, const T* __restrict__ tws) {
-  using F = LineFFT<T, N, RM>;
-  using V = typename Vec2<T>::type;
-  if (ctrl->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  __shared__ T sred[32 * 5];
-  __shared__ int sflag;
-  const int tid = threadIdx.x;
-  const int pairs = blockDim.x / F::TS;
-  const int p = tid % pairs, j = tid / pairs;
-  const int x = blockIdx.x * 2 * pairs + 2 * p;
-  const size_t base = (size_t)blockIdx.y * outer_stride + x;
-  constexpr int LS = line_stride_words<T, N, RM, false>();
-  T* sr = sm + (size_t)p * 2 * LS;
-  T* si = sr + LS;
-  // order 6: xi and dspec of this thread's elements, copied asynchronously
-  // while the forward transform runs ([q][j][p] pairs of columns)
-  V* pre_x = reinterpret_cast<V*>(smem_raw + align16((size_t)pairs * 2 * LS * sizeof(T)));
-  V* pre_d = pre_x + (size_t)N * pairs;
-  T vr[F::R], vi[F::R];
-#pragma unroll
-  for (int q = 0; q < F::R; ++q) {
-    const size_t idx = base + (size_t)(j + q * F::TS) * line_stride;
-    const V v = *reinterpret_cast<const V*>(data + idx);
-    if (ORDER == 6) {
-      const size_t e = (size_t)(q * F::TS + j) * pairs + p;
-      if (sizeof(V) == 8) {
-        cp_async_8(pre_x + e, xi + idx);
-        cp_async_8(pre_d + e, dspec + idx);
-      } else {
-        cp_async_16(pre_x + e, xi + idx);
-        cp_async_16(pre_d + e, dspec + idx);
-      }
-    }
-    vr[q] = v.x;
-    vi[q] = v.y;
-  }
-  F::run(vr, vi, j, sr, si, twc, tws);
-  if (ORDER == 6) cp_async_wait_all();
-
-  const T mo = (symo != nullptr) ? symo[blockIdx.y] : T(0);
-  const T mxa = symx[x] + mo, mxb = symx[x + 1] + mo;
-  const KConst<T>& C = kconst<T>(kp);
-  const T s = C.s, se2 = C.se2, sl = C.sl;
-  const T alpha_prev = (ORDER == 6) ? (T)ctrl->alpha : T(0);
-  T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
-#pragma unroll
-  for (int q = 0; q < F::R; ++q) {
-    const int k = j + q * F::TS;
-    T h[2];
-    dht_split(sr, si, k, N, h[0], h[1]);
-    const T ml = syml[k];
-    T dv[2];
-    if (ORDER == 4) {
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const T mu = (c ? mxb : mxa) + ml;
-        const T dd = h[c] * recip_ge1(T(1) + mu * (s + se2 * mu));
-        dv[c] = dd;
-        acc[0] += h[c] * dd;
-        acc[1] += dd * dd;
-        acc[2] += (mu * dd) * (mu * dd);
-      }
-    } else {
-      // xi holds the transformed part of the residual that is linear in the
-      // iterate and not formed by the stencil kernel: -T_h[u - g] (plain
-      // FP64) or R_outer - T_h[delta] (inner solve); it advances with the
-      // previous step, xi -= alpha_prev T_h d_prev, where dspec keeps the
-      // transform of T_h d_prev.  With L = lam s + s mu + s eps^2 mu^2 + 1/mu,
-      // d = rt / L = mu rt / P and T_h d = d / mu = rt / P, where
-      // P = 1 + mu (lam s + mu (s + s eps^2 mu)) >= 1: one reciprocal.
-      const size_t idx = base + (size_t)k * line_stride;
-      const V xv = pre_x[(size_t)(q * F::TS + j) * pairs + p];
-      const V dp = pre_d[(size_t)(q * F::TS + j) * pairs + p];
-      const T xs[2] = {xv.x, xv.y}, ds[2] = {dp.x, dp.y};
-      T xn[2], tn[2];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const T mu = (c ? mxb : mxa) + ml;
-        T rt = T(0), dd = T(0), xc = T(0), td = T(0);
-        if (mu > T(0)) {
-          xc = xs[c] - alpha_prev * ds[c];
-          rt = h[c] + xc;
-          td = rt * recip_ge1(T(1) + mu * (sl + mu * (s + se2 * mu)));
-          dd = mu * td;
-          acc[3] += dd * td;
-        }
-        xn[c] = xc;
-        tn[c] = td;
-        dv[c] = dd;
-        acc[0] += rt * dd;
-        acc[1] += dd * dd;
-        acc[2] += (mu * dd) * (mu * dd);
-        acc[4] += rt * rt;
-      }
-      V xo, o;
-      xo.x = xn[0];
-      xo.y = xn[1];
-      o.x = tn[0];
-      o.y = tn[1];
-      *reinterpret_cast<V*>(xi + idx) = xo;
-      *reinterpret_cast<V*>(dspec + idx) = o;
-    }
-    vr[q] = dv[0];
-    vi[q] = dv[1];
-  }
-  __syncthreads();  // every thread has read the forward spectrum
-  F::run(vr, vi, j, sr, si, twc, tws);
-  const T scale = C.inv_ntot;
-#pragma unroll
-  for (int q = 0; q < F::R; ++q) {
-    const int k = j + q * F::TS;
-    T h1, h2;
-    dht_split(sr, si, k, N, h1, h2);
-    V o;
-    o.x = h1 * scale;
-    o.y = h2 * scale;
-    *reinterpret_cast<V*>(data + base + (size_t)k * line_stride) = o;
-  }
-
+// Block and grid reduction of the middle pass's five Parseval sums (fixed
+// order) and the last block's bookkeeping: the sums into ctrl, the inner
+// stopping rule on the preconditioned norm, the order-6 residual norm and
+// convergence test, and the reset of the line-search state.
+template <typename T, int ORDER>
+__device__ __forceinline__ void mid_finish(T (&acc)[5], T* sred, double* partials, Ctrl* ctrl, const KParams& kp,
+                                           int* sflag_) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  int& sflag = *sflag_;
   T v[5];
 #pragma unroll
   for (int m = 0; m < 5; ++m) v[m] = acc[m];
@@ -405,7 +290,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 && ORDER == 4 ? 3 : 2
     gather_partials<T, 5, false>(tt, reinterpret_cast<const T*>(partials), sred);
     double tot[5];
     for (int m_ = 0; m_ < 5; ++m_) tot[m_] = (double)tt[m_];
-    if (tid == 0) {
+    if (tid == 0 && ctrl->cg) {
+      // conjugate gradients: z = L_h^{-1} r was just formed; beta = (r, z) /
+      // (r, z)_previous goes to alpha for the direction update p = z + beta p
+      // fused into the next Hessian-vector kernel (beta = 0 on the first pass)
+      const double rz_new = tot[0] * kp.hd * kp.inv_ntot;
+      ctrl->rd = rz_new;
+      ctrl->alpha = (ctrl->rz > 0.0) ? rz_new / ctrl->rz : 0.0;
+      ctrl->rz = rz_new;
+      if (!isfinite(rz_new)) {
+        ctrl->status = 7;
+        ctrl->done = 1;
+      }
+      ctrl->counter[CS_MID] = 0;
+    } else if (tid == 0) {
       const double w = kp.hd * kp.inv_ntot;
       ctrl->rd = tot[0] * w;
       ctrl->dd = tot[1] * w;
@@ -453,9 +351,197 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 && ORDER == 4 ? 3 : 2
       ctrl->c2 = -1.0;
       ctrl->c3 = 0.0;
       ctrl->alpha = 0.0;
+      ctrl->ls_pass = 0;
       ctrl->counter[CS_MID] = 0;
     }
   }
+}
+
+// ------------------------------------------------------------- middle pass
+// Tiles of 2 * pairs x-columns at one outer index (y in 3D), lines along the
+// last axis.  PERSIST (the FP32 passes of the inner iteration): a grid of a
+// few CTAs per SM loops over the tiles, and every thread prefetches, with
+// cp.async into shared memory, its own elements of the next tile's data and
+// of the current tile's xi / dspec, so that loads stay in flight while the
+// transforms of the current tile run (no barrier is needed for the staged
+// data: each thread reads only what it copied).  Otherwise one tile per CTA
+// with direct loads.
+template <typename T, int N, int ORDER, int RM, bool PERSIST>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 && ORDER == 4 && !PERSIST ? 3 : 2)
+    k_mid(T* data, unsigned line_stride, unsigned outer_stride, int ntx, int ntiles, KParams kp, Ctrl* ctrl,
+          double* partials, T* xi, T* dspec, const T* __restrict__ symx, const T* __restrict__ symo,
+          const T* __restrict__ syml, const T* __restrict__ twc, const T* __restrict__ tws) {
+  using F = LineFFT<T, N, RM>;
+  using V = typename Vec2<T>::type;
+  if (ctrl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ T sred[32 * 5];
+  __shared__ int sflag;
+  const int tid = threadIdx.x;
+  const int pairs = blockDim.x / F::TS;
+  const int p = tid % pairs, j = tid / pairs;
+  constexpr int LS = line_stride_words<T, N, RM, false>();
+  T* sr = sm + (size_t)p * 2 * LS;
+  T* si = sr + LS;
+  // staging ([q][j][p] pairs of columns): order 6 xi and dspec of the
+  // current tile, then (PERSIST) two buffers of the data
+  V* pre_x = reinterpret_cast<V*>(smem_raw + align16((size_t)pairs * 2 * LS * sizeof(T)));
+  V* pre_d = pre_x + (size_t)N * pairs;
+  V* pre_w = pre_x + (ORDER == 6 ? 2 : 0) * (size_t)N * pairs;
+  // element offsets in 32 bits: every grid has fewer than 2^32 cells
+  auto elem = [&](int q) { return (unsigned)(q * F::TS + j) * pairs + p; };
+  auto tile_base = [&](int t) {
+    const int xb = t % ntx, yo = t / ntx;
+    return (unsigned)yo * outer_stride + (unsigned)(xb * 2 * pairs + 2 * p);
+  };
+  auto copy_vec = [&](V* dst, const T* src) {
+    if (sizeof(V) == 8)
+      cp_async_8(dst, src);
+    else
+      cp_async_16(dst, src);
+  };
+  const KConst<T>& C = kconst<T>(kp);
+  const T s = C.s, se2 = C.se2, sl = C.sl;
+  const T alpha_prev = (ORDER == 6) ? (T)ctrl->alpha : T(0);
+  T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
+  if (PERSIST && (int)blockIdx.x < ntiles) {
+    const unsigned b0 = tile_base(blockIdx.x);
+#pragma unroll
+    for (int q = 0; q < F::R; ++q) copy_vec(pre_w + elem(q), data + (b0 + (unsigned)(j + q * F::TS) * line_stride));
+    cp_async_commit();
+  }
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int xb = t % ntx, yo = t / ntx;
+    const int x = xb * 2 * pairs + 2 * p;
+    const unsigned base = tile_base(t);
+    V* wst = pre_w + (unsigned)(it & 1) * N * pairs;
+    if (ORDER == 6) {
+#pragma unroll
+      for (int q = 0; q < F::R; ++q) {
+        const unsigned idx = base + (unsigned)(j + q * F::TS) * line_stride;
+        copy_vec(pre_x + elem(q), xi + idx);
+        copy_vec(pre_d + elem(q), dspec + idx);
+      }
+      cp_async_commit();
+    }
+    T vr[F::R], vi[F::R];
+    if (PERSIST) {
+      const int tn = t + gridDim.x;
+      if (tn < ntiles) {
+        const unsigned bn = tile_base(tn);
+        V* wnx = pre_w + (unsigned)((it + 1) & 1) * N * pairs;
+#pragma unroll
+        for (int q = 0; q < F::R; ++q) copy_vec(wnx + elem(q), data + (bn + (unsigned)(j + q * F::TS) * line_stride));
+      }
+      cp_async_commit();
+      // this tile's data is the oldest group in flight
+      if (ORDER == 6)
+        cp_async_wait_group<2>();
+      else
+        cp_async_wait_group<1>();
+#pragma unroll
+      for (int q = 0; q < F::R; ++q) {
+        const V v = wst[elem(q)];
+        vr[q] = v.x;
+        vi[q] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < F::R; ++q) {
+        const V v = *reinterpret_cast<const V*>(data + (base + (unsigned)(j + q * F::TS) * line_stride));
+        vr[q] = v.x;
+        vi[q] = v.y;
+      }
+    }
+    F::run(vr, vi, j, sr, si, twc, tws);
+    if (ORDER == 6) {
+      if (PERSIST)
+        cp_async_wait_group<1>();
+      else
+        cp_async_wait_all();
+    }
+
+    const T mo = (symo != nullptr) ? symo[yo] : T(0);
+    const T mxa = symx[x] + mo, mxb = symx[x + 1] + mo;
+#pragma unroll
+    for (int q = 0; q < F::R; ++q) {
+      const int k = j + q * F::TS;
+      T h[2];
+      dht_split(sr, si, k, N, h[0], h[1]);
+      const T ml = syml[k];
+      T dv[2];
+      if (ORDER == 4) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const T mu = (c ? mxb : mxa) + ml;
+          const T dd = h[c] * recip_ge1(T(1) + mu * (s + se2 * mu));
+          dv[c] = dd;
+          acc[0] += h[c] * dd;
+          acc[1] += dd * dd;
+          acc[2] += (mu * dd) * (mu * dd);
+        }
+      } else {
+        // xi holds the transformed part of the residual that is linear in the
+        // iterate and not formed by the stencil kernel: -T_h[u - g] (plain
+        // FP64) or R_outer - T_h[delta] (inner solve); it advances with the
+        // previous step, xi -= alpha_prev T_h d_prev, where dspec keeps the
+        // transform of T_h d_prev.  With L = lam s + s mu + s eps^2 mu^2 + 1/mu,
+        // d = rt / L = mu rt / P and T_h d = d / mu = rt / P, where
+        // P = 1 + mu (lam s + mu (s + s eps^2 mu)) >= 1: one reciprocal.
+        const unsigned idx = base + (unsigned)k * line_stride;
+        const V xv = pre_x[elem(q)];
+        const V dp = pre_d[elem(q)];
+        const T xs[2] = {xv.x, xv.y}, ds[2] = {dp.x, dp.y};
+        T xn[2], tn[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const T mu = (c ? mxb : mxa) + ml;
+          T rt = T(0), dd = T(0), xc = T(0), td = T(0);
+          if (mu > T(0)) {
+            xc = xs[c] - alpha_prev * ds[c];
+            rt = h[c] + xc;
+            td = rt * recip_ge1(T(1) + mu * (sl + mu * (s + se2 * mu)));
+            dd = mu * td;
+            acc[3] += dd * td;
+          }
+          xn[c] = xc;
+          tn[c] = td;
+          dv[c] = dd;
+          acc[0] += rt * dd;
+          acc[1] += dd * dd;
+          acc[2] += (mu * dd) * (mu * dd);
+          acc[4] += rt * rt;
+        }
+        V xo, o;
+        xo.x = xn[0];
+        xo.y = xn[1];
+        o.x = tn[0];
+        o.y = tn[1];
+        *reinterpret_cast<V*>(xi + idx) = xo;
+        *reinterpret_cast<V*>(dspec + idx) = o;
+      }
+      vr[q] = dv[0];
+      vi[q] = dv[1];
+    }
+    __syncthreads();  // every thread has read the forward spectrum
+    F::run(vr, vi, j, sr, si, twc, tws);
+    const T scale = C.inv_ntot;
+#pragma unroll
+    for (int q = 0; q < F::R; ++q) {
+      const int k = j + q * F::TS;
+      T h1, h2;
+      dht_split(sr, si, k, N, h1, h2);
+      V o;
+      o.x = h1 * scale;
+      o.y = h2 * scale;
+      *reinterpret_cast<V*>(data + (base + (unsigned)k * line_stride)) = o;
+    }
+    __syncthreads();  // the line buffers are rewritten by the next tile
+  }
+  if (PERSIST) cp_async_wait_all();
+  mid_finish<T, ORDER>(acc, sred, partials, ctrl, kp, &sflag);
 }
 
 // ------------------------------------------------------ spectral helpers
@@ -529,22 +615,24 @@ size_t pair_smem() {
 }
 
 // Number of column pairs per block: fill 256 threads, bounded by the shared
-// memory budget and by the available pairs; a power of two.
+// memory budget, by the available pairs and by the autotuner's cap (0: no
+// cap); a power of two.
 template <typename T, int N, int RM, bool ROWS>
-int pick_pairs(int avail_pairs) {
+int pick_pairs(int avail_pairs, int cap = 0) {
   using F = LineFFT<T, N, RM>;
   int pairs = kThreads / F::TS;
   while (pairs > 1 && (size_t)pairs * pair_smem<T, N, RM, ROWS>() > kMaxSmem) pairs >>= 1;
   while (pairs > 1 && pairs > avail_pairs) pairs >>= 1;
+  while (cap > 0 && pairs > 1 && pairs > cap) pairs >>= 1;
   return pairs < 1 ? 1 : pairs;
 }
 
 template <typename S, typename T, int N, typename SI = S>
 cudaError_t rows_impl(const SI* src, S* dst, int nrows, T scale, const int* done, const T* twc,
-                      const T* tws, cudaStream_t st) {
+                      const T* tws, cudaStream_t st, int cap = 0) {
   constexpr int RM = radix_pass<T>();
   using F = LineFFT<T, N, RM>;
-  const int pairs = pick_pairs<T, N, RM, true>(1 << 30);
+  const int pairs = pick_pairs<T, N, RM, true>(1 << 30, cap);
   const int rows_per_block = 2 * pairs;
   const int grid = (nrows + rows_per_block - 1) / rows_per_block;
   k_dht_rows<S, T, N, RM, SI><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, true>(), st>>>(
@@ -554,10 +642,10 @@ cudaError_t rows_impl(const SI* src, S* dst, int nrows, T scale, const int* done
 
 template <typename S, typename T, int N>
 cudaError_t cols_impl(S* data, int nx, int nouter, size_t line_stride, size_t outer_stride, T scale,
-                      const int* done, const T* twc, const T* tws, cudaStream_t st) {
+                      const int* done, const T* twc, const T* tws, cudaStream_t st, int cap = 0) {
   constexpr int RM = radix_pass<T>();
   using F = LineFFT<T, N, RM>;
-  const int pairs = pick_pairs<T, N, RM, false>(nx / 2);
+  const int pairs = pick_pairs<T, N, RM, false>(nx / 2, cap);
   dim3 grid(nx / (2 * pairs), nouter);
   k_dht_cols<S, T, N, RM><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, false>(), st>>>(
       data, line_stride, outer_stride, scale, done, twc, tws);
@@ -568,9 +656,11 @@ template <typename T, int N>
 cudaError_t mid_impl(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* xi, T* dspec,
                      const AxisTables<T>& tb, cudaStream_t st) {
   constexpr int RM = radix_mid<T>();
+  constexpr bool PERSIST = sizeof(T) == 4;
   using F = LineFFT<T, N, RM>;
+  using V = typename Vec2<T>::type;
   const int nx = kp.nx;
-  const int pairs = pick_pairs<T, N, RM, false>(nx / 2);
+  const int pairs = pick_pairs<T, N, RM, false>(nx / 2, tb.tile_cap[2]);
   size_t line_stride, outer_stride;
   int nouter;
   const T* symo;
@@ -594,28 +684,33 @@ cudaError_t mid_impl(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T
     twc = tb.twc[2];
     tws = tb.tws[2];
   }
-  dim3 grid(nx / (2 * pairs), nouter);
-  using V = typename Vec2<T>::type;
-  const size_t sm = kp.order == 6 ? align16(pairs * pair_smem<T, N, RM, false>()) + 2 * (size_t)N * pairs * sizeof(V)
-                                  : pairs * pair_smem<T, N, RM, false>();
+  const int ntx = nx / (2 * pairs);
+  const int ntiles = ntx * nouter;
+  // persistent: the CTAs that __launch_bounds__ keeps resident on every SM
+  const int per_sm = 2;
+  const int grid = PERSIST ? std::min(ntiles, per_sm * kp.nsm) : ntiles;
+  const size_t sm = align16(pairs * pair_smem<T, N, RM, false>()) +
+                    ((kp.order == 6 ? 2 : 0) + (PERSIST ? 2 : 0)) * (size_t)N * pairs * sizeof(V);
   if (sm > kMaxSmemPre) return cudaErrorInvalidConfiguration;
   if (kp.order == 4)
-    k_mid<T, N, 4, RM><<<grid, pairs * F::TS, sm, st>>>(data, line_stride, outer_stride, kp, ctrl, partials,
-                                                   xi, dspec, tb.sym[0], symo, syml, twc, tws);
+    k_mid<T, N, 4, RM, PERSIST><<<grid, pairs * F::TS, sm, st>>>(data, (unsigned)line_stride, (unsigned)outer_stride, ntx, ntiles, kp,
+                                                                 ctrl, partials, xi, dspec, tb.sym[0], symo, syml,
+                                                                 twc, tws);
   else
-    k_mid<T, N, 6, RM><<<grid, pairs * F::TS, sm, st>>>(data, line_stride, outer_stride, kp, ctrl, partials,
-                                                   xi, dspec, tb.sym[0], symo, syml, twc, tws);
+    k_mid<T, N, 6, RM, PERSIST><<<grid, pairs * F::TS, sm, st>>>(data, (unsigned)line_stride, (unsigned)outer_stride, ntx, ntiles, kp,
+                                                                 ctrl, partials, xi, dspec, tb.sym[0], symo, syml,
+                                                                 twc, tws);
   return cudaGetLastError();
 }
-
 
 template <typename T, int N>
 void set_attrs_T() {
   constexpr int RP = radix_pass<T>(), RD = radix_mid<T>();
   cudaFuncSetAttribute(k_dht_rows<T, T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   cudaFuncSetAttribute(k_dht_cols<T, T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_mid<T, N, 4, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-  cudaFuncSetAttribute(k_mid<T, N, 6, RD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPre);
+  constexpr bool PST = sizeof(T) == 4;
+  cudaFuncSetAttribute(k_mid<T, N, 4, RD, PST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPre);
+  cudaFuncSetAttribute(k_mid<T, N, 6, RD, PST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPre);
 }
 
 #define PSD_DISPATCH_N(n, CALL)      \
@@ -637,7 +732,7 @@ void set_attrs_T() {
 template <typename T>
 cudaError_t launch_dht_rows(const T* src, T* dst, int nx, int nrows, T scale, const int* done,
                             const AxisTables<T>& tb, cudaStream_t st) {
-  PSD_DISPATCH_N(nx, (rows_impl<T, T, NN>(src, dst, nrows, scale, done, tb.twc[0], tb.tws[0], st)));
+  PSD_DISPATCH_N(nx, (rows_impl<T, T, NN>(src, dst, nrows, scale, done, tb.twc[0], tb.tws[0], st, tb.tile_cap[0])));
 }
 
 template <typename T>
@@ -656,7 +751,7 @@ cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const i
     nouter = kp.ny;
   }
   PSD_DISPATCH_N(n, (cols_impl<T, T, NN>(data, kp.nx, nouter, line_stride, outer_stride, scale, done,
-                                         tb.twc[ax], tb.tws[ax], st)));
+                                         tb.twc[ax], tb.tws[ax], st, tb.tile_cap[1])));
 }
 
 template <typename T>

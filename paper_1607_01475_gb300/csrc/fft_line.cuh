@@ -44,6 +44,43 @@ __device__ __forceinline__ ff half_of<ff>(ff x) {
   return ff_scale2(x, 0.5f);
 }
 
+// a * b + c and c - a * b with one rounding where the type allows it.
+template <typename T>
+__device__ __forceinline__ T mul_add(T a, T b, T c) {
+  return a * b + c;
+}
+template <>
+__device__ __forceinline__ float mul_add<float>(float a, float b, float c) {
+  return fmaf(a, b, c);
+}
+template <>
+__device__ __forceinline__ double mul_add<double>(double a, double b, double c) {
+  return fma(a, b, c);
+}
+template <typename T>
+__device__ __forceinline__ T neg_mul_add(T a, T b, T c) {
+  return c - a * b;
+}
+template <>
+__device__ __forceinline__ float neg_mul_add<float>(float a, float b, float c) {
+  return fmaf(-a, b, c);
+}
+template <>
+__device__ __forceinline__ double neg_mul_add<double>(double a, double b, double c) {
+  return fma(-a, b, c);
+}
+
+// Twiddle source: (cos, sin)(2 pi t / N) from two tables of the element type.
+template <typename T>
+struct TwPair {
+  const T* __restrict__ c;
+  const T* __restrict__ s;
+  __device__ __forceinline__ void get(int t, T& cv, T& sv) const {
+    cv = ld_tw(c + t);
+    sv = ld_tw(s + t);
+  }
+};
+
 // cos(2 pi m / 16), the 16th roots of unity (exact values of cos(pi/8),
 // sin(pi/8) and sqrt(2)/2).
 __host__ __device__ constexpr double cos16(int m) {
@@ -84,17 +121,21 @@ struct DFT {
     DFT<R / 2>::run(orr, oi);
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) {
+      if (4 * k == R) {  // W = -i: (tr, ti) = (oi, -orr)
+        re[k] = er[k] + oi[k];
+        im[k] = ei[k] - orr[k];
+        re[k + R / 2] = er[k] - oi[k];
+        im[k + R / 2] = ei[k] + orr[k];
+        continue;
+      }
       T tr, ti;
       if (k == 0) {
         tr = orr[k];
         ti = oi[k];
-      } else if (4 * k == R) {  // W = -i
-        tr = oi[k];
-        ti = -orr[k];
       } else {  // W = c - i sn
         const T c = (T)cos16(k * 16 / R), sn = (T)sin16(k * 16 / R);
-        tr = orr[k] * c + oi[k] * sn;
-        ti = oi[k] * c - orr[k] * sn;
+        tr = mul_add(oi[k], sn, orr[k] * c);
+        ti = neg_mul_add(orr[k], sn, oi[k] * c);
       }
       re[k] = er[k] + tr;
       im[k] = ei[k] + ti;
@@ -125,9 +166,8 @@ struct LineFFT {
   static constexpr int L = N + N / 16;
   __device__ __forceinline__ static int pix(int i) { return i + (i >> 4); }
 
-  template <int NS>
-  __device__ __forceinline__ static void pass(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si,
-                                              const T* __restrict__ twc, const T* __restrict__ tws) {
+  template <int NS, typename Tw>
+  __device__ __forceinline__ static void pass(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si, const Tw& tw) {
     constexpr int RP = (N / NS >= R) ? R : N / NS;
     constexpr int M = R / RP;
 #pragma unroll
@@ -144,10 +184,11 @@ struct LineFFT {
 #pragma unroll
         for (int r = 1; r < RP; ++r) {
           const int t = jm * r * (N / (NS * RP));
-          const T c = ld_tw(twc + t), sn = ld_tw(tws + t);
+          T c, sn;
+          tw.get(t, c, sn);
           const T a = xr[r], bb = xi[r];
-          xr[r] = a * c + bb * sn;
-          xi[r] = bb * c - a * sn;
+          xr[r] = mul_add(bb, sn, a * c);
+          xi[r] = neg_mul_add(a, sn, bb * c);
         }
       }
       DFT<RP>::run(xr, xi);
@@ -160,9 +201,8 @@ struct LineFFT {
     }
   }
 
-  template <int NS>
-  __device__ __forceinline__ static void rest(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si,
-                                              const T* __restrict__ twc, const T* __restrict__ tws) {
+  template <int NS, typename Tw>
+  __device__ __forceinline__ static void rest(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si, const Tw& tw) {
     if constexpr (NS < N) {
       constexpr int RP = (N / NS >= R) ? R : N / NS;
       __syncthreads();
@@ -172,16 +212,20 @@ struct LineFFT {
         vi[q] = si[pix(j + q * TS)];
       }
       __syncthreads();
-      pass<NS>(vr, vi, j, sr, si, twc, tws);
-      rest<NS * RP>(vr, vi, j, sr, si, twc, tws);
+      pass<NS>(vr, vi, j, sr, si, tw);
+      rest<NS * RP>(vr, vi, j, sr, si, tw);
     }
   }
 
+  template <typename Tw>
+  __device__ __forceinline__ static void run_tw(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si, const Tw& tw) {
+    pass<1>(vr, vi, j, sr, si, tw);
+    rest<R>(vr, vi, j, sr, si, tw);
+    __syncthreads();
+  }
   __device__ __forceinline__ static void run(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si,
                                              const T* __restrict__ twc, const T* __restrict__ tws) {
-    pass<1>(vr, vi, j, sr, si, twc, tws);
-    rest<R>(vr, vi, j, sr, si, twc, tws);
-    __syncthreads();
+    run_tw(vr, vi, j, sr, si, TwPair<T>{twc, tws});
   }
 };
 

@@ -20,30 +20,31 @@ void set_attrs_ff() {
 }  // namespace
 
 cudaError_t launch_dht_rows_ff(const double* src, ff* dst, int nx, int nrows, const AxisTables<ff>& tb,
-                               cudaStream_t st) {
-  PSD_DISPATCH_N(nx, (rows_impl<ff, ff, NN, double>(src, dst, nrows, ff(1.0f, 0.0f), nullptr, tb.twc[0], tb.tws[0],
+                               cudaStream_t st, const int* skip) {
+  PSD_DISPATCH_N(nx, (rows_impl<ff, ff, NN, double>(src, dst, nrows, ff(1.0f, 0.0f), skip, tb.twc[0], tb.tws[0],
                                                      st)));
 }
 
-cudaError_t launch_dht_cols_ff(ff* data, const KParams& kp, int ax, const AxisTables<ff>& tb, cudaStream_t st) {
+cudaError_t launch_dht_cols_ff(ff* data, const KParams& kp, int ax, const AxisTables<ff>& tb, cudaStream_t st,
+                               const int* skip) {
   const ff scale(1.0f, 0.0f);
   const int n = ax == 1 ? kp.ny : kp.nz;
   const size_t line_stride = ax == 1 ? (size_t)kp.nx : (size_t)kp.nx * kp.ny;
   const size_t outer_stride = ax == 1 ? (size_t)kp.nx * kp.ny : (size_t)kp.nx;
   const int nouter = ax == 1 ? kp.nz : kp.ny;
-  PSD_DISPATCH_N(n, (cols_impl<ff, ff, NN>(data, kp.nx, nouter, line_stride, outer_stride, scale, nullptr,
+  PSD_DISPATCH_N(n, (cols_impl<ff, ff, NN>(data, kp.nx, nouter, line_stride, outer_stride, scale, skip,
                                            tb.twc[ax], tb.tws[ax], st)));
 }
 
 cudaError_t launch_dht_rows_ff_from_f32(const float* src, ff* dst, int nx, int nrows, const AxisTables<ff>& tb,
-                                        cudaStream_t st) {
-  PSD_DISPATCH_N(nx, (rows_impl<ff, ff, NN, float>(src, dst, nrows, ff(1.0f, 0.0f), nullptr, tb.twc[0], tb.tws[0],
+                                        cudaStream_t st, const int* skip) {
+  PSD_DISPATCH_N(nx, (rows_impl<ff, ff, NN, float>(src, dst, nrows, ff(1.0f, 0.0f), skip, tb.twc[0], tb.tws[0],
                                                     st)));
 }
 
 template <int N>
 cudaError_t last_ff_impl(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
-                         double* partials, const AxisTables<ff>& tb, cudaStream_t st, double* dc) {
+                         double* partials, const AxisTables<ff>& tb, cudaStream_t st, double* dc, const int* skip) {
   constexpr int RM = radix_pass<ff>();
   using F = LineFFT<ff, N, RM>;
   const int nx = kp.nx;
@@ -60,18 +61,19 @@ cudaError_t last_ff_impl(const ff* data, double* theta, float* out32, const KPar
   if (out32 == nullptr)
     k_dht_last_ff<N, RM, EPI_THETA><<<grid, pairs * F::TS, sm, st>>>(data, theta, out32, line_stride, outer_stride,
                                                                     kp, ctrl, partials, tb.twc[ax], tb.tws[ax],
-                                                                    tb.sym[0], symo, tb.sym[ax], dc);
+                                                                    tb.sym[0], symo, tb.sym[ax], dc, skip);
   else
     k_dht_last_ff<N, RM, EPI_RESID><<<grid, pairs * F::TS, sm, st>>>(data, theta, out32, line_stride, outer_stride,
                                                                     kp, ctrl, partials, tb.twc[ax], tb.tws[ax],
-                                                                    tb.sym[0], symo, tb.sym[ax], nullptr);
+                                                                    tb.sym[0], symo, tb.sym[ax], nullptr, skip);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
-                               double* partials, const AxisTables<ff>& tb, cudaStream_t st, double* dc) {
+                               double* partials, const AxisTables<ff>& tb, cudaStream_t st, double* dc,
+                               const int* skip) {
   const int n = kp.dim == 3 ? kp.nz : kp.ny;
-  PSD_DISPATCH_N(n, (last_ff_impl<NN>(data, theta, out32, kp, ctrl, partials, tb, st, dc)));
+  PSD_DISPATCH_N(n, (last_ff_impl<NN>(data, theta, out32, kp, ctrl, partials, tb, st, dc, skip)));
 }
 
 

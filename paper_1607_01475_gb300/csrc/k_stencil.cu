@@ -154,13 +154,90 @@ __global__ void k_round_f32(float* out, const double* in, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
 }
-__global__ void k_accumulate_f64(double* u, const float* delta, float* u32, size_t n, const double* dsum) {
+__global__ void k_accumulate_f64(double* u, const float* delta, float* u32, size_t n, const double* dsum,
+                                 const int* skip) {
+  if (skip != nullptr && *skip) return;
   const double m = dsum ? *dsum / (double)n : 0.0;  // mean of delta, removed
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double v = u[i] + ((double)delta[i] - m);
     u[i] = v;
     u32[i] = (float)v;
   }
+}
+
+// One conjugate-gradient update of the adjoint solve H lambda = b:
+// lam += alpha p, r -= alpha q (q = H p), w = r (the preconditioner's input,
+// transformed in place), with ||r||_2 = (h^d sum r^2)^{1/2}, the iteration
+// count and the stopping test (ctrl->tol absolute, ctrl->max_iter) in the
+// last block.  Returns at once when ctrl->done is set.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_cg_update(T* lam, const T* p, T* r, const T* q, T* w, size_t n, double hd,
+                                                  Ctrl* ctrl, double* partials) {
+  __shared__ T sred[32];
+  __shared__ int sflag;
+  if (ctrl->done) return;
+  const T al = (T)ctrl->alpha;
+  T acc = T(0);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T ri = r[i] - al * q[i];
+    lam[i] += al * p[i];
+    r[i] = ri;
+    w[i] = ri;
+    acc += ri * ri;
+  }
+  T v[1] = {acc};
+  block_reduce<T, 1, false>(v, sred);
+  if (publish_and_check_last<T>(v, 1, reinterpret_cast<T*>(partials), &ctrl->counter[CS_MISC], &sflag)) {
+    T tt[1];
+    gather_partials<T, 1, false>(tt, reinterpret_cast<const T*>(partials), sred);
+    if (threadIdx.x == 0) {
+      const double res = sqrt((double)tt[0] * hd);
+      const int it = ctrl->iter + 1;
+      ctrl->iter = it;
+      ctrl->res_l2 = res;
+      if (!isfinite(res)) {
+        ctrl->status = 7;
+        ctrl->done = 1;
+      } else if (res <= ctrl->tol) {
+        ctrl->status = 0;
+        ctrl->done = 1;
+      } else if (it >= ctrl->max_iter) {
+        ctrl->status = 4;
+        ctrl->done = 1;
+      }
+      ctrl->counter[CS_MISC] = 0;
+    }
+  }
+}
+
+// Outer residual of the mixed adjoint solve: out32 = (float)(b - q) with
+// (h^d sum (b - q)^2)^{1/2} into ctrl->res_l2 (FP64).
+__global__ void __launch_bounds__(NT) k_sub_round(const double* b, const double* q, float* out32, size_t n, double hd,
+                                                  Ctrl* ctrl, double* partials) {
+  __shared__ double sred[32];
+  __shared__ int sflag;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double e = b[i] - q[i];
+    out32[i] = (float)e;
+    acc += e * e;
+  }
+  double v[1] = {acc};
+  block_reduce<double, 1, false>(v, sred);
+  if (publish_and_check_last<double>(v, 1, partials, &ctrl->counter[CS_MISC], &sflag)) {
+    double tt[1];
+    gather_partials<double, 1, false>(tt, partials, sred);
+    if (threadIdx.x == 0) {
+      ctrl->res_l2 = sqrt(tt[0] * hd);
+      ctrl->counter[CS_MISC] = 0;
+    }
+  }
+}
+
+// y += (double) x (FP64 accumulation of an FP32 correction).
+__global__ void k_add_f32(double* y, const float* x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] += (double)x[i];
 }
 
 // Thin-film right-hand side f = u - s Delta_h^v u (Sec. 6.1, Eq.
@@ -332,6 +409,26 @@ cudaError_t launch_linesearch(const T* u, const T* ubase, const T* d, int pk, co
 }
 
 template <typename T>
+cudaError_t launch_cg_update(T* lam, const T* p, T* r, const T* q, T* w, size_t n, double hd, Ctrl* ctrl,
+                             double* partials, cudaStream_t st) {
+  k_cg_update<T><<<std::min(grid1d(n), 1024), NT, 0, st>>>(lam, p, r, q, w, n, hd, ctrl, partials);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cg_update<float>(float*, const float*, float*, const float*, float*, size_t, double,
+                                             Ctrl*, double*, cudaStream_t);
+template cudaError_t launch_cg_update<double>(double*, const double*, double*, const double*, double*, size_t,
+                                              double, Ctrl*, double*, cudaStream_t);
+cudaError_t launch_sub_round(const double* b, const double* q, float* out32, size_t n, double hd, Ctrl* ctrl,
+                             double* partials, cudaStream_t st) {
+  k_sub_round<<<std::min(grid1d(n), 1024), NT, 0, st>>>(b, q, out32, n, hd, ctrl, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_f32(double* y, const float* x, size_t n, cudaStream_t st) {
+  k_add_f32<<<grid1d(n), 256, 0, st>>>(y, x, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_axpby(T* y, const T* x, const T* z, double a, double b, double c, size_t n, cudaStream_t st) {
   k_axpby<T><<<grid1d(n), 256, 0, st>>>(y, x, z, a, b, c, n);
   return cudaGetLastError();
@@ -371,8 +468,8 @@ cudaError_t launch_round_f32(float* out, const double* in, size_t n, cudaStream_
   return cudaGetLastError();
 }
 cudaError_t launch_accumulate_f64(double* u, const float* delta, float* u32, size_t n, const double* dsum,
-                                  cudaStream_t st) {
-  k_accumulate_f64<<<grid1d(n), 256, 0, st>>>(u, delta, u32, n, dsum);
+                                  cudaStream_t st, const int* skip) {
+  k_accumulate_f64<<<grid1d(n), 256, 0, st>>>(u, delta, u32, n, dsum, skip);
   return cudaGetLastError();
 }
 

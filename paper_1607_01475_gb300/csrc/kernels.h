@@ -14,6 +14,10 @@ struct AxisTables {
   const T* twc[3];  // cos(2 pi t / n_a), t < n_a
   const T* tws[3];  // sin(2 pi t / n_a)
   const T* sym[3];  // (4/h^2) sin^2(pi k / n_a), k < n_a
+  // tile widths chosen by the autotuner: at most this many line pairs per
+  // block in the row, strided and middle passes (0: as many as fill 256
+  // threads)
+  int tile_cap[3];
 };
 
 // ----------------------------------------------------------------- DHT passes
@@ -32,18 +36,21 @@ cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const i
 // double-word twiddles).  Between passes the data stays in float-float form
 // (hi, lo pairs in the 8 bytes of an FP64 element): the x pass reads FP64
 // (or FP32) and writes pairs; the strided pass transforms pairs in place.
+// skip (device, may be null): the pass returns at once when *skip != 0.
 cudaError_t launch_dht_rows_ff(const double* src, ff* dst, int nx, int nrows, const AxisTables<ff>& tb,
-                               cudaStream_t st);
+                               cudaStream_t st, const int* skip = nullptr);
 cudaError_t launch_dht_rows_ff_from_f32(const float* src, ff* dst, int nx, int nrows, const AxisTables<ff>& tb,
-                                        cudaStream_t st);
-cudaError_t launch_dht_cols_ff(ff* data, const KParams& kp, int ax, const AxisTables<ff>& tb, cudaStream_t st);
+                                        cudaStream_t st, const int* skip = nullptr);
+cudaError_t launch_dht_cols_ff(ff* data, const KParams& kp, int ax, const AxisTables<ff>& tb, cudaStream_t st,
+                               const int* skip = nullptr);
 // The last pass (z in 3D, y in 2D) with a fused epilogue: out32 == nullptr:
 // theta += DHT(data) / mu, and (dc != null) *dc = the zero-frequency
 // coefficient (the sum of the transformed field); else out32 = (float)(DHT(data)
 // - theta) and ctrl->res_l2 = its Parseval norm (h^d / N sum)^{1/2}.  mu = 0
 // gives 0.
 cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, const KParams& kp, Ctrl* ctrl,
-                               double* partials, const AxisTables<ff>& tb, cudaStream_t st, double* dc = nullptr);
+                               double* partials, const AxisTables<ff>& tb, cudaStream_t st, double* dc = nullptr,
+                               const int* skip = nullptr);
 
 // The middle pass along the slowest axis (y in 2D, z in 3D) of the
 // preconditioner: forward DHT, division by the symbol of L_h, Parseval sums
@@ -87,6 +94,9 @@ struct ResArgs {
   int fluxff;      // FP64 plain without d, p = 4, 3D: fixed-point linear part and
                    // float-float flux (see k_res3d_col)
   int fxs;         // with fluxff: the fixed-point scale S (u = q 2^-S), in [15, 120]
+  const int* fxs_dev;  // or (non-null) S read from device memory at launch: the fixed-point
+                       // variant and the plain FP64 kernel are both launched and the one that
+                       // does not apply (S outside [15, 120] / inside) returns at once
 };
 
 // r = f - N_h^{loc}[u_in + alpha d] (plain) or
@@ -128,6 +138,46 @@ cudaError_t launch_spec_quad(const T* a, const KParams& kp, Ctrl* ctrl, double* 
 // partial sum record per block); fp32 = (T is float).
 long long residual_grid_blocks(const KParams& kp, bool fp32);
 
+// ------------------------------------------------- device-side loop control
+// The conditional handles of CUDA graph WHILE nodes are set by these
+// single-thread kernels at the end of each loop body.
+// Loop while !c->done and the body count stays below guard_max (the guard
+// trips PSD_ERR_NOCONV).
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, Ctrl* c, int guard_max, cudaStream_t st);
+// General-p line search: another Newton pass while the bracket has not
+// converged (c->c3 == 0), the run is not done, and fewer than max_passes ran.
+cudaError_t launch_ls_cond(cudaGraphConditionalHandle h, Ctrl* c, int max_passes, cudaStream_t st);
+// dst = src where c->iter is odd (the iterate ends in the second ping-pong buffer).
+template <typename T>
+cudaError_t launch_copy_if_odd(T* dst, const T* src, const Ctrl* c, size_t n, cudaStream_t st);
+// Mixed solve, after each FP64 outer residual (norm in c2->res_l2): count it,
+// decide convergence / failure into c3, and either stop the inner solve
+// (c->done = 1) or initialise it from the template tmpl with max_iter =
+// min(max_iter - inner_total, inner_cap).  cond: the outer WHILE handle.
+cudaError_t launch_mixed_check(Ctrl* c3, const Ctrl* c2, Ctrl* c, const Ctrl* tmpl, double tol, int max_iter,
+                               int max_outer, int inner_cap, int order6, cudaStream_t st);
+// Mixed solve, after the inner solve: inner_total += c->iter, last alpha,
+// non-finite inner residual -> c3 failed (done).
+cudaError_t launch_mixed_after(Ctrl* c3, const Ctrl* c, cudaStream_t st);
+// Mixed solve: the choice of the fixed-point / float-float FP64 residual
+// (the host rule of the direct solve, on device) from the max |G|^2 and
+// max|u| estimates in c2 (res_linf, res_l2) into c3->fxs.
+cudaError_t launch_fluxff_decide(Ctrl* c3, const Ctrl* c2, double sqrt_vol, double cdiv, double tol, cudaStream_t st);
+// c = a fresh control block (tol -1, no iteration limit), on device.
+cudaError_t launch_ctrl_reset(Ctrl* c, cudaStream_t st);
+
+// ------------------------------------------------------------ adjoint CG
+// lam += alpha p, r -= alpha q, w = r; ||r||_2, iteration count and stopping
+// test into ctrl (alpha = ctrl->alpha); no-op once ctrl->done is set.
+template <typename T>
+cudaError_t launch_cg_update(T* lam, const T* p, T* r, const T* q, T* w, size_t n, double hd, Ctrl* ctrl,
+                             double* partials, cudaStream_t st);
+// out32 = (float)(b - q), ||b - q||_2 into ctrl->res_l2.
+cudaError_t launch_sub_round(const double* b, const double* q, float* out32, size_t n, double hd, Ctrl* ctrl,
+                             double* partials, cudaStream_t st);
+// y += (double) x.
+cudaError_t launch_add_f32(double* y, const float* x, size_t n, cudaStream_t st);
+
 // ------------------------------------------------------------------ misc
 // y = a * x + b * z + c elementwise (x or z may be null = 0; may alias y).
 template <typename T>
@@ -142,7 +192,7 @@ cudaError_t launch_round_f32(float* out, const double* in, size_t n, cudaStream_
 // u += delta - mean(delta) (dsum: device pointer to sum(delta), or null for
 // no mean removal), u32 = (float) u.
 cudaError_t launch_accumulate_f64(double* u, const float* delta, float* u32, size_t n, const double* dsum,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const int* skip = nullptr);
 
 void init_dht_attributes();
 

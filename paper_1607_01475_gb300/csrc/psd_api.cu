@@ -16,7 +16,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <array>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -32,7 +35,10 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int kChunk = 8;          // iterations enqueued between host checks
+constexpr int kChunk = 8;          // iterations enqueued between host checks (direct mode)
+constexpr int kBody = 2;           // iterations per WHILE-loop body of a captured solve
+static_assert(kBody % 2 == 0, "a loop body must start and end on the same ping-pong parity");
+constexpr int kCapDepth = 3;       // nesting of WHILE loops: outer, inner, general-p line search
 static_assert(kChunk % 2 == 0, "a chunk must start and end on the same ping-pong parity");
 constexpr int kLsPassesGen = 16;   // Newton passes of the general-p line search
 constexpr double kInnerEta = 1e-4;  // inner FP32 solve: relative drop of the preconditioned norm
@@ -64,6 +70,10 @@ struct psd_context {
   double* Dsp = nullptr;    // order 6: DHT spectrum of T_h d for the last direction d
   double* Ftf = nullptr;    // time loops: right-hand side f of the current step
   double* Gtf = nullptr;    // SPFC time loop: g = u^n of the current step
+  double* adj_q = nullptr;  // adjoint CG: H p (FP64), second direction buffer, copy of u
+  double* adj_pb = nullptr;
+  double* adj_u = nullptr;
+  float* adj32[2] = {nullptr, nullptr};  // mixed adjoint: FP32 correction, H p
   // FP32 work arrays (mixed)
   float* u32 = nullptr;
   float* da = nullptr;
@@ -76,6 +86,8 @@ struct psd_context {
   double* partials = nullptr;
   Ctrl* ctrl = nullptr;   // PSD run state
   Ctrl* ctrl2 = nullptr;  // auxiliary reductions (outer residual, norms)
+  Ctrl* ctrl3 = nullptr;  // mixed solve: outer-loop state of the captured solve
+  Ctrl* ctrl_tmpl = nullptr;  // mixed solve: control block of a fresh inner solve
   Ctrl* h_ctrl = nullptr; // pinned host mirror
 
   double* d_hist = nullptr;
@@ -98,13 +110,17 @@ struct psd_context {
   long long prof_n[PSD_PROF_CLASSES] = {};
   std::vector<float> prof_durs[PSD_PROF_CLASSES];  // per-launch durations (ms)
 
-  // CUDA graphs of one chunk of iterations, captured on a private stream and
-  // replayed on st: the mixed inner chunk (all arguments are the handle's
-  // own buffers) and the FP64 chunk (keyed on the caller's u, f, g)
+  // The whole solve as one CUDA graph (its loops are WHILE conditional
+  // nodes), captured on private streams and replayed on st; keyed on the
+  // caller's u, f, g.
   cudaStream_t gst = nullptr;
-  cudaGraphExec_t g_inner = nullptr;
-  cudaGraphExec_t g_fp64 = nullptr;
-  const void* g_fp64_key[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t capst[kCapDepth] = {};
+  int cap_depth = 0;
+  bool capturing = false;
+  cudaGraphExec_t g_solve = nullptr;
+  const void* g_solve_key[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t g_cg32 = nullptr;  // adjoint CG chunks: FP32 (mixed inner, own buffers)
+  cudaGraphExec_t g_cg64 = nullptr;  // and FP64 (own buffers: u is copied in)
   bool graphs_off = false;  // a capture failed once: launch directly from then on
 };
 
@@ -382,20 +398,22 @@ psd_status full_dht(psd_context* c, T* x, T scale, const AxisTables<T>& tb) {
 }
 
 // theta += DHT(v) / mu (order 6, mixed): v is src64 (FP64, transformed in
-// place) or src32 (FP32, transformed into D); theta lives in Z.
-psd_status dht_theta_ff(psd_context* c, const double* src64, const float* src32, double* dc = nullptr) {
+// place) or src32 (FP32, transformed into D); theta lives in Z.  skip
+// (device, may be null): the passes return at once when *skip != 0.
+psd_status dht_theta_ff(psd_context* c, const double* src64, const float* src32, double* dc = nullptr,
+                        const int* skip = nullptr) {
   const KParams& kp = c->kp;
   const int nrows = kp.ny * kp.nz;
   psd::ff* x = reinterpret_cast<psd::ff*>(c->D);  // float-float pairs between the passes
   if (src32) {
     ProfScope p_(c, PSD_PROF_DHT_ROWS_FF);
-    CK(psd::launch_dht_rows_ff_from_f32(src32, x, kp.nx, nrows, c->tbff, c->st));
+    CK(psd::launch_dht_rows_ff_from_f32(src32, x, kp.nx, nrows, c->tbff, c->st, skip));
   } else {
     ProfScope p_(c, PSD_PROF_DHT_ROWS_FF);
-    CK(psd::launch_dht_rows_ff(src64, x, kp.nx, nrows, c->tbff, c->st));
+    CK(psd::launch_dht_rows_ff(src64, x, kp.nx, nrows, c->tbff, c->st, skip));
   }
-  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, c->tbff, c->st)); }
-  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(x, c->Z, nullptr, kp, nullptr, c->partials, c->tbff, c->st, dc)); }
+  if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, c->tbff, c->st, skip)); }
+  { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(x, c->Z, nullptr, kp, nullptr, c->partials, c->tbff, c->st, dc, skip)); }
   return PSD_OK;
 }
 
@@ -413,10 +431,104 @@ psd_status precond_passes(psd_context* c, T* W, T* D, Ctrl* ctrl, T* xi, T* dspe
   return PSD_OK;
 }
 
+// ------------------------------------------------------ graph capture
+// Stream of nesting depth d for capturing the bodies of WHILE nodes (depth 0
+// is the graph itself, captured on gst).
+psd_status cap_stream(psd_context* c, int d, cudaStream_t* out) {
+  if (d <= 0) {
+    if (!c->gst) CK(cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking));
+    *out = c->gst;
+    return PSD_OK;
+  }
+  if (d > kCapDepth) return fail(c, PSD_ERR_CUDA, "graph loops nested too deep");
+  if (!c->capst[d - 1]) CK(cudaStreamCreateWithFlags(&c->capst[d - 1], cudaStreamNonBlocking));
+  *out = c->capst[d - 1];
+  return PSD_OK;
+}
+
+// Insert a WHILE conditional node at the current position of the capture on
+// c->st and capture its body: body(handle) enqueues on c->st (a stream of the
+// next depth) and must end with a kernel that sets the condition.  The body
+// runs at least once (default condition 1).
+template <typename Body>
+psd_status capture_while(psd_context* c, Body&& body) {
+  cudaStream_t s = c->st, s2 = nullptr;
+  TRY(cap_stream(c, c->cap_depth + 1, &s2));
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return fail(c, PSD_ERR_CUDA, "capture_while outside a capture");
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+  CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t bg = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(s2, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  c->st = s2;
+  ++c->cap_depth;
+  psd_status r = body(h);
+  --c->cap_depth;
+  c->st = s;
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s2, &out);
+  if (r != PSD_OK) return r;
+  if (e != cudaSuccess) return fail(c, PSD_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  return PSD_OK;
+}
+
+// Capture enqueue() (which enqueues on c->st) into a graph and instantiate
+// it into *exec.  Any failure leaves *exec null and returns the status.
+template <typename Enq>
+psd_status capture_graph(psd_context* c, cudaGraphExec_t* exec, Enq&& enqueue) {
+  cudaStream_t s = nullptr;
+  TRY(cap_stream(c, 0, &s));
+  cudaStream_t saved = c->st;
+  c->st = s;
+  c->cap_depth = 0;
+  cudaGraph_t g = nullptr;
+  psd_status r = PSD_ERR_CUDA;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    r = enqueue();
+    if (cudaStreamEndCapture(s, &g) != cudaSuccess) g = nullptr;
+  }
+  c->st = saved;
+  if (r != PSD_OK || g == nullptr || cudaGraphInstantiate(exec, g, 0) != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    *exec = nullptr;
+    return r != PSD_OK ? r : fail(c, PSD_ERR_CUDA, "graph capture or instantiation failed");
+  }
+  cudaGraphDestroy(g);
+  return PSD_OK;
+}
+
+// The line search of one iteration: one pass (p = 4, 6), or for a general p
+// one safeguarded Newton pass per launch -- a fixed run of kLsPassesGen
+// launches (each returns at once after convergence) when enqueued directly,
+// a WHILE loop that stops at convergence inside a captured graph.
 template <typename T>
 psd_status linesearch(psd_context* c, const T* u, const T* ubase, const T* D, Ctrl* ctrl) {
-  const int passes = (c->pk == psd::PK_GEN) ? kLsPassesGen : 1;
-  for (int i = 0; i < passes; ++i) {
+  if (c->pk != psd::PK_GEN) {
+    ProfScope p_(c, cls_of<T>(PSD_PROF_LINESEARCH_FP64));
+    CK(psd::launch_linesearch<T>(u, ubase, D, c->pk, c->kp, ctrl, c->partials, c->st));
+    return PSD_OK;
+  }
+  if (c->capturing) {
+    return capture_while(c, [&](cudaGraphConditionalHandle h) -> psd_status {
+      CK(psd::launch_linesearch<T>(u, ubase, D, c->pk, c->kp, ctrl, c->partials, c->st));
+      CK(psd::launch_ls_cond(h, ctrl, kLsPassesGen, c->st));
+      return PSD_OK;
+    });
+  }
+  for (int i = 0; i < kLsPassesGen; ++i) {
     ProfScope p_(c, cls_of<T>(PSD_PROF_LINESEARCH_FP64));
     CK(psd::launch_linesearch<T>(u, ubase, D, c->pk, c->kp, ctrl, c->partials, c->st));
   }
@@ -475,15 +587,23 @@ psd_status use_fluxff(psd_context* c, int* fxs) {
   return PSD_OK;
 }
 
-// FP64 residual r = f - N_h[u] into r (order 6: P0[...] including T_h[u - g]),
-// norms into ctrl2 (res_l2, res_linf).  Uses W, Z as scratch (order 6).
-psd_status residual64(psd_context* c, const double* u, const double* f, const double* g, double* r,
-                      int fxs = 0) {
+// Whether the FP64 outer residuals of this handle may take the fixed-point /
+// float-float variant at all (the per-iterate bound is checked on device in
+// graph mode, by use_fluxff in direct mode).
+bool fluxff_eligible(const psd_context* c) {
   const KParams& kp = c->kp;
-  Ctrl h;
-  init_ctrl(h, -1.0, 1 << 30);
-  TRY(upload_ctrl(c, c->ctrl2, h));
-  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, r, kp.order == 4 ? 1 : 0, 0, fxs ? 1 : 0, fxs};
+  return c->pk == psd::PK_4 && kp.dim == 3 && kp.nx >= 32 && kp.ny >= 8 && c->prm.tol > 0;
+}
+
+// FP64 residual r = f - N_h[u] into r (order 6: P0[...] including T_h[u - g]),
+// norms into ctrl2 (res_l2, res_linf), all enqueued (ctrl2 reset on device).
+// fxs: fixed-point scale from the host (direct mode); fxs_dev: from device
+// memory (graph mode).  Uses W, Z as scratch (order 6).
+psd_status residual64(psd_context* c, const double* u, const double* f, const double* g, double* r, int fxs = 0,
+                      const int* fxs_dev = nullptr) {
+  const KParams& kp = c->kp;
+  CK(psd::launch_ctrl_reset(c->ctrl2, c->st));
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, r, kp.order == 4 ? 1 : 0, 0, fxs ? 1 : 0, fxs, fxs_dev};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
   if (kp.order == 6) {
     // r <- P0[r_loc - T_h[u - g]] through the spectrum
@@ -500,29 +620,112 @@ psd_status residual64(psd_context* c, const double* u, const double* f, const do
 // Sixth-order outer residual in the transform domain (mixed precision):
 // R32 <- (float) DHT(P0[f - N_h^{loc}[u]] - T_h[u - g]) = DHT(r_loc) - theta
 // with theta = DHT(T_h[u - g]) in Z (the subtraction, the rounding and the
-// Parseval norm fused into the last transform pass); ||R||_2 into *res.
-psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f, double* res, int fxs) {
+// Parseval norm fused into the last transform pass); ||R||_2 into
+// ctrl2->res_l2 (enqueued).
+psd_status outer_residual6_spec(psd_context* c, const double* u, const double* f, int fxs,
+                                const int* fxs_dev = nullptr) {
   const KParams& kp = c->kp;
-  Ctrl h;
-  init_ctrl(h, -1.0, 1 << 30);
-  TRY(upload_ctrl(c, c->ctrl2, h));
-  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0, fxs ? 1 : 0, fxs};
+  CK(psd::launch_ctrl_reset(c->ctrl2, c->st));
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, 0, 0, fxs ? 1 : 0, fxs, fxs_dev};
   { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl2, c->partials, c->st)); }
   const int nrows = kp.ny * kp.nz;
   psd::ff* x = reinterpret_cast<psd::ff*>(c->W);  // transformed in place, float-float pairs after the x pass
   { ProfScope p_(c, PSD_PROF_DHT_ROWS_FF); CK(psd::launch_dht_rows_ff(c->W, x, kp.nx, nrows, c->tbff, c->st)); }
   if (kp.dim == 3) { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_cols_ff(x, kp, 1, c->tbff, c->st)); }
   { ProfScope p_(c, PSD_PROF_DHT_COLS_FF); CK(psd::launch_dht_last_ff(x, c->Z, c->R32, kp, c->ctrl2, c->partials, c->tbff, c->st)); }
-  Ctrl h2;
-  TRY(read_ctrl(c, c->ctrl2, h2));
-  *res = h2.res_l2;
+  return PSD_OK;
+}
+
+// ------------------------------------------------------------- plain FP64
+// The part of the FP64 solve before the loop: order 6 xi_0 = DHT(-T_h[u0 -
+// g]) = -DHT(u0 - g) / mu (direction spectrum 0), then the initial residual.
+psd_status fp64_start(psd_context* c, const double* f, const double* g, double* u) {
+  const KParams& kp = c->kp;
+  if (kp.order == 6) {
+    CK(cudaMemsetAsync(c->Dsp, 0, c->N * sizeof(double), c->st));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
+    TRY(full_dht<double>(c, c->Z, 1.0, c->tb64));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec_apply_T<double>(c->Z, -1.0, kp, c->tb64, c->st)); }
+  }
+  ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, kp.order == 4 ? 1 : 0, 0};
+  { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl, c->partials, c->st)); }
+  return PSD_OK;
+}
+
+// count (even) FP64 PSD iterations from u (iterates ping-pong between u and
+// ub: an even count starts and ends on u).
+psd_status fp64_iterations(psd_context* c, const double* f, double* u, int count) {
+  const KParams& kp = c->kp;
+  for (int i = 0; i < count; ++i) {
+    double* cur = (i % 2 == 0) ? u : c->ub;
+    double* nxt = (i % 2 == 0) ? c->ub : u;
+    TRY(precond_passes<double>(c, c->W, c->D, c->ctrl, c->Z, c->Dsp, c->tb64));
+    TRY(linesearch<double>(c, cur, nullptr, c->D, c->ctrl));
+    ResArgs<double> a{cur, c->D, nxt, f, nullptr, c->W, kp.order == 4 ? 1 : 0, 1};
+    { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl, c->partials, c->st)); }
+  }
+  return PSD_OK;
+}
+
+// The whole FP64 solve after the control block upload, as graph work: the
+// start, a WHILE loop of kBody iterations per body, and the copy of an odd
+// final iterate back into u.
+psd_status fp64_graph_body(psd_context* c, const double* f, const double* g, double* u) {
+  TRY(fp64_start(c, f, g, u));
+  const int guard = c->prm.max_iter / kBody + 3;
+  TRY(capture_while(c, [&](cudaGraphConditionalHandle h) -> psd_status {
+    TRY(fp64_iterations(c, f, u, kBody));
+    CK(psd::launch_loop_cond(h, c->ctrl, guard, c->st));
+    return PSD_OK;
+  }));
+  CK(psd::launch_copy_if_odd<double>(u, c->ub, c->ctrl, c->N, c->st));
+  return PSD_OK;
+}
+
+void fill_info(psd_info* info, int iters, int outer, double res, double resinf, double alpha, float ms, int status) {
+  if (!info) return;
+  info->iters = iters;
+  info->outer_iters = outer;
+  info->res_l2 = res;
+  info->res_linf = resinf;
+  info->energy = NAN;
+  info->last_alpha = alpha;
+  info->wall_ms = ms;
+  info->status = status;
+}
+
+// Launch the cached graph of this handle's solve for the key (u, f, g),
+// capturing it first if needed; false in *ran when graphs are off (direct
+// mode) or the capture failed (then direct mode from now on).
+template <typename Enq>
+psd_status launch_solve_graph(psd_context* c, const double* f, const double* g, double* u, bool* ran, Enq&& enq) {
+  *ran = false;
+  if (c->prof || c->graphs_off) return PSD_OK;
+  if (c->g_solve && (c->g_solve_key[0] != u || c->g_solve_key[1] != f || c->g_solve_key[2] != g)) {
+    cudaGraphExecDestroy(c->g_solve);
+    c->g_solve = nullptr;
+  }
+  if (!c->g_solve) {
+    c->capturing = true;
+    const psd_status s = capture_graph(c, &c->g_solve, enq);
+    c->capturing = false;
+    if (s != PSD_OK || !c->g_solve) {
+      c->graphs_off = true;
+      c->err.clear();
+      return PSD_OK;
+    }
+    c->g_solve_key[0] = u;
+    c->g_solve_key[1] = f;
+    c->g_solve_key[2] = g;
+  }
+  CK(cudaGraphLaunch(c->g_solve, c->st));
+  *ran = true;
   return PSD_OK;
 }
 
 // Plain FP64 PSD.
 psd_status solve_fp64(psd_context* c, const double* f, const double* g, double* u, psd_info* info) {
   TRY(ensure_fp64(c));
-  const KParams& kp = c->kp;
   Ctrl h;
   init_ctrl(h, c->prm.tol, c->prm.max_iter);
   if (c->hist_cap > 0) {
@@ -532,125 +735,216 @@ psd_status solve_fp64(psd_context* c, const double* f, const double* g, double* 
   }
   TRY(upload_ctrl(c, c->ctrl, h));
   CK(cudaEventRecord(c->ev0, c->st));
-  if (kp.order == 6) {
-    // xi_0 = DHT(-T_h[u0 - g]) = -DHT(u0 - g) / mu; the direction spectrum starts at 0
-    CK(cudaMemsetAsync(c->Dsp, 0, c->N * sizeof(double), c->st));
-    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->Z, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
-    TRY(full_dht<double>(c, c->Z, 1.0, c->tb64));
-    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_spec_apply_T<double>(c->Z, -1.0, kp, c->tb64, c->st)); }
-  }
-  {
-    ResArgs<double> a{u, nullptr, nullptr, f, nullptr, c->W, kp.order == 4 ? 1 : 0, 0};
-    { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl, c->partials, c->st)); }
-  }
-  int k = 0;
+  bool ran = false;
+  TRY(launch_solve_graph(c, f, g, u, &ran, [&]() { return fp64_graph_body(c, f, g, u); }));
   Ctrl hc;
-  // a chunk always starts at an even k (kChunk is even), so one graph serves
-  // every chunk
-  auto chunk = [&]() -> psd_status {
-    for (int i = 0; i < kChunk; ++i) {
-      double* cur = (i % 2 == 0) ? u : c->ub;
-      double* nxt = (i % 2 == 0) ? c->ub : u;
-      TRY(precond_passes<double>(c, c->W, c->D, c->ctrl, c->Z, c->Dsp, c->tb64));
-      TRY(linesearch<double>(c, cur, nullptr, c->D, c->ctrl));
-      ResArgs<double> a{cur, c->D, nxt, f, nullptr, c->W, kp.order == 4 ? 1 : 0, 1};
-      { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_PLAIN, c->pk, kp, c->ctrl, c->partials, c->st)); }
+  if (!ran) {
+    // direct: chunks of kChunk iterations, the stop flag read after each
+    TRY(fp64_start(c, f, g, u));
+    int k = 0;
+    for (;;) {
+      TRY(fp64_iterations(c, f, u, kChunk));
+      k += kChunk;
+      TRY(read_ctrl(c, c->ctrl, hc));
+      if (hc.done) break;
+      if (k > c->prm.max_iter + 2 * kChunk) {  // host-side guard: never loop unbounded
+        hc.status = PSD_ERR_NOCONV;
+        break;
+      }
     }
-    return PSD_OK;
-  };
-  if (c->g_fp64 && (c->g_fp64_key[0] != u || c->g_fp64_key[1] != f || c->g_fp64_key[2] != g)) {
-    cudaGraphExecDestroy(c->g_fp64);
-    c->g_fp64 = nullptr;
-  }
-  c->g_fp64_key[0] = u;
-  c->g_fp64_key[1] = f;
-  c->g_fp64_key[2] = g;
-  for (;;) {
-    TRY(run_chunk(c, &c->g_fp64, chunk));
-    k += kChunk;
-    TRY(read_ctrl(c, c->ctrl, hc));
-    if (hc.done) break;
-    if (k > c->prm.max_iter + 2 * kChunk) {  // host-side guard: never loop unbounded
-      hc.status = PSD_ERR_NOCONV;
-      break;
-    }
+    if (hc.iter % 2 == 1) CK(cudaMemcpyAsync(u, c->ub, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   }
   CK(cudaEventRecord(c->ev1, c->st));
-  if (hc.iter % 2 == 1) CK(cudaMemcpyAsync(u, c->ub, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-  CK(cudaStreamSynchronize(c->st));
+  TRY(read_ctrl(c, c->ctrl, hc));
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-  if (info) {
-    info->iters = hc.iter;
-    info->outer_iters = 0;
-    info->res_l2 = hc.res_l2;
-    info->res_linf = hc.res_linf;
-    info->energy = NAN;
-    info->last_alpha = hc.alpha;
-    info->wall_ms = ms;
-    info->status = hc.status;
-  }
+  fill_info(info, hc.iter, 0, hc.res_l2, hc.res_linf, hc.alpha, ms, hc.status);
   return (psd_status)hc.status;
 }
 
+// ------------------------------------------------------------------ mixed
 // Mixed precision: outer FP64 residual R = f - N_h[u] (order 6: P0[...]
 // with the exact T_h[u - g]); inner FP32 PSD on the correction delta with
 // residual R - (N_h[u + delta] - N_h[u]) (order 6: mean-projected, the T_h
 // term kept as the DHT spectrum of delta); u += delta in FP64.
+//
+// The FP32 inner iterations (count even) of one inner solve.
+psd_status inner_iterations(psd_context* c, int count) {
+  const KParams& kp = c->kp;
+  const bool six = kp.order == 6;
+  const float* rphys = six ? nullptr : c->R32;
+  for (int i = 0; i < count; ++i) {
+    float* cur = (i % 2 == 0) ? c->da : c->db;
+    float* nxt = (i % 2 == 0) ? c->db : c->da;
+    TRY(precond_passes<float>(c, c->W32, c->D32, c->ctrl, six ? c->R32 : nullptr, c->Dsp32, c->tb32));
+    TRY(linesearch<float>(c, cur, c->u32, c->D32, c->ctrl));
+    ResArgs<float> a{cur, c->D32, nxt, rphys, c->u32, c->W32, six ? 0 : 1, 1};
+    { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_INNER, c->pk, kp, c->ctrl, c->partials, c->st)); }
+  }
+  return PSD_OK;
+}
+
+// The start of an inner solve: delta = 0, the direction spectrum 0 (order
+// 6), and the inner residual at delta = 0.
+psd_status inner_start(psd_context* c) {
+  const KParams& kp = c->kp;
+  const bool six = kp.order == 6;
+  CK(cudaMemsetAsync(c->da, 0, c->N * sizeof(float), c->st));
+  if (six) CK(cudaMemsetAsync(c->Dsp32, 0, c->N * sizeof(float), c->st));
+  // order 6: the outer residual enters in the middle pass as the initial xi
+  // (R32 holds its spectrum and is advanced in place by the inner solve)
+  ResArgs<float> a{c->da, nullptr, nullptr, six ? nullptr : c->R32, c->u32, c->W32, six ? 0 : 1, 0};
+  { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_INNER, c->pk, kp, c->ctrl, c->partials, c->st)); }
+  return PSD_OK;
+}
+
+// The control block of an inner FP32 solve.  The FP32 residual of
+// s eps^2 Delta_h^2 delta carries rounding noise of order eps32 * 64 s eps^2
+// / h^4 * |delta|, which on fine grids is as large as the residual itself,
+// so ||r||_2 cannot serve as the inner stopping test.  The preconditioned
+// norm (r, L_h^{-1} r)^{1/2} damps that noise by the symbol of L_h; the inner
+// solve stops when it has dropped by inner_eta, or when it has stopped
+// halving (its FP32 floor).
+void inner_ctrl(psd_context* c, Ctrl& h, int max_iter) {
+  init_ctrl(h, 0.0, max_iter);
+  h.pre_eta = c->prm.inner_eta > 0.0 ? c->prm.inner_eta : kInnerEta;
+  h.pre_stall_max = c->prm.inner_stall > 0 ? c->prm.inner_stall : kInnerStall;
+}
+
+// Order 6: the problem lives on mean(u) = mean(g); project u0 once (host).
+psd_status mixed_project_mean(psd_context* c, const double* g, double* u) {
+  const KParams& kp = c->kp;
+  Ctrl hg, hu;
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(g, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+  TRY(read_ctrl(c, c->ctrl2, hg));
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+  TRY(read_ctrl(c, c->ctrl2, hu));
+  const double shift = (hg.rd - hu.rd) / (double)c->N;
+  if (shift != 0.0) {
+    ProfScope p_(c, PSD_PROF_OTHER);
+    CK(psd::launch_axpby<double>(u, u, nullptr, 1.0, 0.0, shift, c->N, c->st));
+  }
+  return PSD_OK;
+}
+
+// The device part of the mixed solve's start: u32 = fl32(u); order 6:
+// theta = DHT(T_h[u0 - g]) (advanced with DHT(T_h delta) after every
+// correction).
+psd_status mixed_start(psd_context* c, const double* g, double* u) {
+  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
+  if (c->kp.order == 6) {
+    CK(cudaMemsetAsync(c->Z, 0, c->N * sizeof(double), c->st));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->D, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
+    TRY(dht_theta_ff(c, c->D, nullptr));
+  }
+  return PSD_OK;
+}
+
+// The whole mixed solve after the host uploads, as graph work: an outer
+// WHILE loop (device decisions in ctrl3) around the FP64 outer residual, the
+// inner FP32 solve (an inner WHILE loop) and the FP64 accumulation.
+psd_status mixed_graph_body(psd_context* c, const double* f, const double* g, double* u) {
+  const KParams& kp = c->kp;
+  const bool six = kp.order == 6;
+  const bool elig = fluxff_eligible(c);
+  TRY(mixed_start(c, g, u));
+  const int guard_outer = std::max(c->prm.max_outer, 1) + 3;
+  const int inner_cap = std::min(std::max(c->prm.max_iter, 1), kInnerMaxIter);
+  const int guard_inner = inner_cap / kBody + 3;
+  return capture_while(c, [&](cudaGraphConditionalHandle ho) -> psd_status {
+    const int* fxs_dev = nullptr;
+    if (elig) {
+      CK(psd::launch_ctrl_reset(c->ctrl2, c->st));
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_gradmax(c->u32, kp, c->ctrl2, c->partials, c->st)); }
+      CK(psd::launch_fluxff_decide(c->ctrl3, c->ctrl2, std::sqrt((double)c->N * kp.hd), kp.cdiv, c->prm.tol, c->st));
+      fxs_dev = &c->ctrl3->fxs;
+    }
+    if (six) {
+      TRY(outer_residual6_spec(c, u, f, 0, fxs_dev));
+    } else {
+      TRY(residual64(c, u, f, g, c->W, 0, fxs_dev));
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->R32, c->W, c->N, c->st)); }
+    }
+    CK(psd::launch_mixed_check(c->ctrl3, c->ctrl2, c->ctrl, c->ctrl_tmpl, c->prm.tol, c->prm.max_iter,
+                               c->prm.max_outer, kInnerMaxIter, six ? 1 : 0, c->st));
+    TRY(inner_start(c));
+    TRY(capture_while(c, [&](cudaGraphConditionalHandle hi) -> psd_status {
+      TRY(inner_iterations(c, kBody));
+      CK(psd::launch_loop_cond(hi, c->ctrl, guard_inner, c->st));
+      return PSD_OK;
+    }));
+    CK(psd::launch_copy_if_odd<float>(c->da, c->db, c->ctrl, c->N, c->st));
+    CK(psd::launch_mixed_after(c->ctrl3, c->ctrl, c->st));
+    // order 6: theta += DHT(T_h delta) with sum(delta) recorded; u += delta
+    // (mean removed for order 6), u32 = fl32(u) -- skipped once the outer
+    // loop is done
+    double* dsum = six ? &c->ctrl2->c3 : nullptr;
+    if (six) TRY(dht_theta_ff(c, nullptr, c->da, dsum, &c->ctrl3->done));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, c->da, c->u32, c->N, dsum, c->st, &c->ctrl3->done)); }
+    CK(psd::launch_loop_cond(ho, c->ctrl3, guard_outer, c->st));
+    (void)inner_cap;
+    return PSD_OK;
+  });
+}
+
 psd_status solve_mixed(psd_context* c, const double* f, const double* g, double* u, psd_info* info) {
   TRY(ensure_fp64(c));
   TRY(ensure_fp32(c));
   const KParams& kp = c->kp;
   const bool six = kp.order == 6;
   CK(cudaEventRecord(c->ev0, c->st));
-  if (six) {
-    // the sixth-order problem lives on mean(u) = mean(g): project u0 once
-    Ctrl hg, hu;
-    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(g, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
-    TRY(read_ctrl(c, c->ctrl2, hg));
-    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
-    TRY(read_ctrl(c, c->ctrl2, hu));
-    const double shift = (hg.rd - hu.rd) / (double)c->N;
-    if (shift != 0.0) {
-      ProfScope p_(c, PSD_PROF_OTHER);
-      CK(psd::launch_axpby<double>(u, u, nullptr, 1.0, 0.0, shift, c->N, c->st));
-    }
+  if (six) TRY(mixed_project_mean(c, g, u));
+  // device state of the graph-driven loops: the outer decisions (ctrl3) and
+  // the template of an inner solve's control block
+  {
+    Ctrl h3;
+    init_ctrl(h3, -1.0, 1 << 30);
+    h3.status = PSD_ERR_NOCONV;
+    TRY(upload_ctrl(c, c->ctrl3, h3));
+    Ctrl ht;
+    inner_ctrl(c, ht, 0);
+    TRY(upload_ctrl(c, c->ctrl_tmpl, ht));
   }
-  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
-  if (six) {
-    // theta = DHT(T_h[u0 - g]), advanced with DHT(T_h delta) after every correction
-    CK(cudaMemsetAsync(c->Z, 0, c->N * sizeof(double), c->st));
-    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(c->D, u, g, 1.0, -1.0, 0.0, c->N, c->st)); }
-    TRY(dht_theta_ff(c, c->D, nullptr));
+  bool ran = false;
+  TRY(launch_solve_graph(c, f, g, u, &ran, [&]() { return mixed_graph_body(c, f, g, u); }));
+  if (ran) {
+    CK(cudaEventRecord(c->ev1, c->st));
+    Ctrl h3;
+    TRY(read_ctrl(c, c->ctrl3, h3));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    fill_info(info, h3.inner_total, h3.outer, h3.res_l2, h3.res_linf, h3.last_alpha, ms, h3.status);
+    return (psd_status)h3.status;
   }
+  // direct: the same steps with the decisions on the host
+  TRY(mixed_start(c, g, u));
   int inner_total = 0, outer = 0;
   int status = PSD_ERR_NOCONV;
   double res = NAN, resinf = -1, last_alpha = 0;
-  const float* delta = nullptr;
+  bool have_delta = false;
   for (;;) {
-    if (delta) {
+    if (have_delta) {
       // order 6: theta += DHT(T_h delta); the zero-frequency coefficient of the
       // transform, sum(delta), is recorded on the device and the accumulation
       // removes the mean of delta, which is zero only up to FP32 rounding,
       // so that mean(u) = mean(g) holds throughout
       double* dsum = six ? &c->ctrl2->c3 : nullptr;
-      if (six) TRY(dht_theta_ff(c, nullptr, delta, dsum));
-      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, delta, c->u32, c->N, dsum, c->st)); }
+      if (six) TRY(dht_theta_ff(c, nullptr, c->da, dsum));
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_accumulate_f64(u, c->da, c->u32, c->N, dsum, c->st)); }
     }
     int fxs = 0;
     TRY(use_fluxff(c, &fxs));
     if (six) {
       // the outer residual stays in the transform domain; the inner solve adds
       // it to its own transformed residual in the middle pass
-      TRY(outer_residual6_spec(c, u, f, &res, fxs));
-      resinf = -1.0;
+      TRY(outer_residual6_spec(c, u, f, fxs));
     } else {
       TRY(residual64(c, u, f, g, c->W, fxs));
-      Ctrl h2;
-      TRY(read_ctrl(c, c->ctrl2, h2));
-      res = h2.res_l2;
-      resinf = h2.res_linf;
     }
+    Ctrl h2;
+    TRY(read_ctrl(c, c->ctrl2, h2));
+    res = h2.res_l2;
+    resinf = six ? -1.0 : h2.res_linf;
     ++outer;
     if (!six) { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->R32, c->W, c->N, c->st)); }
     if (!std::isfinite(res)) {
@@ -665,42 +959,14 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
       status = PSD_ERR_NOCONV;
       break;
     }
-    // The FP32 residual of s eps^2 Delta_h^2 delta carries rounding noise of
-    // order eps32 * 64 s eps^2 / h^4 * |delta|, which on fine grids is as large
-    // as the residual itself, so ||r||_2 cannot serve as the inner stopping
-    // test.  The preconditioned norm (r, L_h^{-1} r)^{1/2} damps that noise by
-    // the symbol of L_h; the inner solve stops when it has dropped by
-    // kInnerEta, or when it has stopped halving (its FP32 floor).
     Ctrl h;
-    init_ctrl(h, 0.0, std::min(c->prm.max_iter - inner_total, kInnerMaxIter));
-    h.pre_eta = c->prm.inner_eta > 0.0 ? c->prm.inner_eta : kInnerEta;
-    h.pre_stall_max = c->prm.inner_stall > 0 ? c->prm.inner_stall : kInnerStall;
+    inner_ctrl(c, h, std::min(c->prm.max_iter - inner_total, kInnerMaxIter));
     TRY(upload_ctrl(c, c->ctrl, h));
-    CK(cudaMemsetAsync(c->da, 0, c->N * sizeof(float), c->st));
-    if (six) CK(cudaMemsetAsync(c->Dsp32, 0, c->N * sizeof(float), c->st));
-    const int norm = six ? 0 : 1;
-    // order 6: the outer residual enters in the middle pass as the initial xi
-    // (R32 holds its spectrum and is advanced in place by the inner solve)
-    const float* rphys = six ? nullptr : c->R32;
-    {
-      ResArgs<float> a{c->da, nullptr, nullptr, rphys, c->u32, c->W32, norm, 0};
-      { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_INNER, c->pk, kp, c->ctrl, c->partials, c->st)); }
-    }
+    TRY(inner_start(c));
     int k = 0;
     Ctrl hc;
-    auto chunk = [&]() -> psd_status {
-      for (int i = 0; i < kChunk; ++i) {
-        float* cur = (i % 2 == 0) ? c->da : c->db;
-        float* nxt = (i % 2 == 0) ? c->db : c->da;
-        TRY(precond_passes<float>(c, c->W32, c->D32, c->ctrl, six ? c->R32 : nullptr, c->Dsp32, c->tb32));
-        TRY(linesearch<float>(c, cur, c->u32, c->D32, c->ctrl));
-        ResArgs<float> a{cur, c->D32, nxt, rphys, c->u32, c->W32, norm, 1};
-        { ProfScope p_(c, PSD_PROF_RESIDUAL_FP32); CK(psd::launch_residual<float>(a, psd::RM_INNER, c->pk, kp, c->ctrl, c->partials, c->st)); }
-      }
-      return PSD_OK;
-    };
     for (;;) {
-      TRY(run_chunk(c, &c->g_inner, chunk));
+      TRY(inner_iterations(c, kChunk));
       k += kChunk;
       TRY(read_ctrl(c, c->ctrl, hc));
       if (hc.done) break;
@@ -712,24 +978,193 @@ psd_status solve_mixed(psd_context* c, const double* f, const double* g, double*
       status = PSD_ERR_NONFINITE;
       break;
     }
-    delta = (hc.iter % 2 == 0) ? c->da : c->db;
-    if (hc.iter == 0) delta = nullptr;
+    if (hc.iter % 2 == 1) CK(cudaMemcpyAsync(c->da, c->db, c->N * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+    have_delta = hc.iter > 0;
   }
   CK(cudaEventRecord(c->ev1, c->st));
   CK(cudaStreamSynchronize(c->st));
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-  if (info) {
-    info->iters = inner_total;
-    info->outer_iters = outer;
-    info->res_l2 = res;
-    info->res_linf = resinf;
-    info->energy = NAN;
-    info->last_alpha = last_alpha;
-    info->wall_ms = ms;
-    info->status = status;
-  }
+  fill_info(info, inner_total, outer, res, resinf, last_alpha, ms, status);
   return (psd_status)status;
+}
+
+// ------------------------------------------------------------- autotuner
+// Tile widths (line pairs per block) of the FP32 row, strided and middle
+// passes of a mixed-precision handle: each pass in turn, every candidate
+// cap is timed on the handle's own buffers (kernel times do not depend on
+// the values) over a few preconditioner solves, and the fastest is kept.
+// Results are cached for the process by (dim, n, order).
+std::mutex g_tune_mu;
+std::map<std::array<int, 5>, std::array<int, 3>> g_tune_cache;
+
+psd_status autotune(psd_context* c) {
+  if (c->prm.precision != PSD_MIXED) return PSD_OK;
+  const KParams& kp = c->kp;
+  const std::array<int, 5> key = {kp.dim, kp.nx, kp.ny, kp.nz, kp.order};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      for (int k = 0; k < 3; ++k) c->tb32.tile_cap[k] = it->second[k];
+      return PSD_OK;
+    }
+  }
+  TRY(ensure_fp32(c));
+  const bool six = kp.order == 6;
+  const size_t bytes = c->N * sizeof(float);
+  CK(cudaMemsetAsync(c->W32, 0, bytes, c->st));
+  CK(cudaMemsetAsync(c->R32, 0, bytes, c->st));
+  if (six) CK(cudaMemsetAsync(c->Dsp32, 0, bytes, c->st));
+  Ctrl h;
+  init_ctrl(h, -1.0, 1 << 30);
+  TRY(upload_ctrl(c, c->ctrl2, h));
+  const bool prof = c->prof;
+  c->prof = false;
+  auto run = [&](int reps, float* ms) -> psd_status {
+    for (int r = 0; r < reps; ++r)
+      TRY(precond_passes<float>(c, c->W32, c->D32, c->ctrl2, six ? c->R32 : nullptr, c->Dsp32, c->tb32));
+    if (ms) {
+      CK(cudaEventRecord(c->ev0, c->st));
+      for (int r = 0; r < reps; ++r)
+        TRY(precond_passes<float>(c, c->W32, c->D32, c->ctrl2, six ? c->R32 : nullptr, c->Dsp32, c->tb32));
+      CK(cudaEventRecord(c->ev1, c->st));
+      CK(cudaEventSynchronize(c->ev1));
+      CK(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+    }
+    return PSD_OK;
+  };
+  static const int kCaps[] = {0, 16, 8, 4, 2, 1};
+  psd_status st = PSD_OK;
+  for (int pass = 0; pass < 3 && st == PSD_OK; ++pass) {
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int cap : kCaps) {
+      c->tb32.tile_cap[pass] = cap;
+      float ms = 0.f;
+      st = run(5, &ms);
+      if (st != PSD_OK) break;
+      if (ms < 0.97f * best_ms) {  // a clear gain over the previous best
+        best_ms = ms;
+        best = cap;
+      }
+    }
+    c->tb32.tile_cap[pass] = best;
+  }
+  c->prof = prof;
+  TRY(st);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {c->tb32.tile_cap[0], c->tb32.tile_cap[1], c->tb32.tile_cap[2]};
+  return PSD_OK;
+}
+
+// ------------------------------------------------ batch (internal hooks)
+// The host part of a solve before its graph work: control blocks uploaded
+// (and, order 6 mixed, the mean projection of u0).
+psd_status solve_prepare(psd_context* c, const double* f, const double* g, double* u) {
+  TRY(ensure_fp64(c));
+  if (c->prm.precision == PSD_MIXED) {
+    TRY(ensure_fp32(c));
+    if (c->kp.order == 6) TRY(mixed_project_mean(c, g, u));
+    Ctrl h3;
+    init_ctrl(h3, -1.0, 1 << 30);
+    h3.status = PSD_ERR_NOCONV;
+    TRY(upload_ctrl(c, c->ctrl3, h3));
+    Ctrl ht;
+    inner_ctrl(c, ht, 0);
+    TRY(upload_ctrl(c, c->ctrl_tmpl, ht));
+  } else {
+    Ctrl h;
+    init_ctrl(h, c->prm.tol, c->prm.max_iter);
+    TRY(upload_ctrl(c, c->ctrl, h));
+  }
+  (void)f;
+  return PSD_OK;
+}
+
+// The solve's graph work enqueued on st (inside a capture), bracketed by the
+// handle's timing events (recorded as event nodes of the graph).
+psd_status solve_capture(psd_context* c, const double* f, const double* g, double* u, cudaStream_t st) {
+  cudaStream_t saved = c->st;
+  c->st = st;
+  c->cap_depth = 0;
+  c->capturing = true;
+  psd_status s = PSD_OK;
+  if (cudaEventRecordWithFlags(c->ev0, st, cudaEventRecordExternal) != cudaSuccess) s = PSD_ERR_CUDA;
+  if (s == PSD_OK)
+    s = (c->prm.precision == PSD_MIXED) ? mixed_graph_body(c, f, g, u) : fp64_graph_body(c, f, g, u);
+  if (s == PSD_OK && cudaEventRecordWithFlags(c->ev1, st, cudaEventRecordExternal) != cudaSuccess) s = PSD_ERR_CUDA;
+  c->capturing = false;
+  c->st = saved;
+  return s;
+}
+
+// The statistics of a solve whose graph work has completed.
+psd_status solve_finish(psd_context* c, psd_info* info) {
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  if (c->prm.precision == PSD_MIXED) {
+    Ctrl h3;
+    TRY(read_ctrl(c, c->ctrl3, h3));
+    fill_info(info, h3.inner_total, h3.outer, h3.res_l2, h3.res_linf, h3.last_alpha, ms, h3.status);
+    return (psd_status)h3.status;
+  }
+  Ctrl hc;
+  TRY(read_ctrl(c, c->ctrl, hc));
+  fill_info(info, hc.iter, 0, hc.res_l2, hc.res_linf, hc.alpha, ms, hc.status);
+  return (psd_status)hc.status;
+}
+
+// Preconditioned conjugate gradients for H x = b in precision T, H = dN_h/du
+// at `base` (order 4; the second variation of Sec. 5.3, symmetric positive
+// definite), preconditioned by the FFT solve of L_h (the PSD search-direction
+// operator).  Device resident: alpha, beta, (r, z) and the stop flag live in
+// ctrl, the direction update p = z + beta p is fused into the Hessian-vector
+// kernel, and chunks of kChunk iterations are replayed from a CUDA graph,
+// the host reading the stop flag once per chunk.  x is zeroed first; r, q,
+// w, z, pa, pb are work arrays (b may alias r).  Stops when ||r||_2 <=
+// tol_abs or after max_iter iterations.
+template <typename T>
+psd_status cg_solve(psd_context* c, const T* base, const T* b, T* x, T* r, T* q, T* w, T* z, T* pa, T* pb,
+                    const AxisTables<T>& tb, double tol_abs, int max_iter, cudaGraphExec_t* cache, Ctrl* out) {
+  const KParams& kp = c->kp;
+  const size_t bytes = c->N * sizeof(T);
+  Ctrl h;
+  init_ctrl(h, tol_abs, max_iter);
+  h.cg = 1;
+  h.rz = 0.0;
+  TRY(upload_ctrl(c, c->ctrl, h));
+  CK(cudaMemsetAsync(x, 0, bytes, c->st));
+  CK(cudaMemsetAsync(pa, 0, bytes, c->st));  // p_0 = 0, so p_1 = z_0
+  if (r != b) CK(cudaMemcpyAsync(r, b, bytes, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(w, b, bytes, cudaMemcpyDeviceToDevice, c->st));
+  TRY(precond_passes<T>(c, w, z, c->ctrl, nullptr, nullptr, tb));  // z_0, (r_0, z_0), beta = 0
+  auto chunk = [&]() -> psd_status {
+    for (int i = 0; i < kChunk; ++i) {
+      T* pold = (i % 2 == 0) ? pa : pb;
+      T* pnew = (i % 2 == 0) ? pb : pa;
+      // p_new = z + beta p_old (fused) and q = H p_new, alpha = (r, z) / (p, q)
+      ResArgs<T> a{z, pold, pnew, nullptr, base, q, 0, 0};
+      { ProfScope p_(c, cls_of<T>(PSD_PROF_RESIDUAL_FP64)); CK(psd::launch_residual<T>(a, psd::RM_HVP, c->pk, kp, c->ctrl, c->partials, c->st)); }
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_cg_update<T>(x, pnew, r, q, w, c->N, kp.hd, c->ctrl, c->partials, c->st)); }
+      TRY(precond_passes<T>(c, w, z, c->ctrl, nullptr, nullptr, tb));  // z = L_h^{-1} r, beta
+    }
+    return PSD_OK;
+  };
+  int k = 0;
+  Ctrl hc;
+  for (;;) {
+    TRY(run_chunk(c, cache, chunk));
+    k += kChunk;
+    TRY(read_ctrl(c, c->ctrl, hc));
+    if (hc.done) break;
+    if (k > max_iter + 2 * kChunk) {  // host-side guard: never loop unbounded
+      hc.status = PSD_ERR_NOCONV;
+      break;
+    }
+  }
+  *out = hc;
+  return PSD_OK;
 }
 
 // E_h[u] (Sec. 5.3 / 5.4 discrete energies; order 6 in the u = nu + gbar
@@ -834,7 +1269,10 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
   if ((s = alloc(c, &c->partials, npart)) != PSD_OK) return bail(s);
   if ((s = alloc(c, &c->ctrl, 1)) != PSD_OK) return bail(s);
   if ((s = alloc(c, &c->ctrl2, 1)) != PSD_OK) return bail(s);
-  if (cudaMemset(c->ctrl, 0, sizeof(Ctrl)) != cudaSuccess || cudaMemset(c->ctrl2, 0, sizeof(Ctrl)) != cudaSuccess) {
+  if ((s = alloc(c, &c->ctrl3, 1)) != PSD_OK) return bail(s);
+  if ((s = alloc(c, &c->ctrl_tmpl, 1)) != PSD_OK) return bail(s);
+  if (cudaMemset(c->ctrl, 0, sizeof(Ctrl)) != cudaSuccess || cudaMemset(c->ctrl2, 0, sizeof(Ctrl)) != cudaSuccess ||
+      cudaMemset(c->ctrl3, 0, sizeof(Ctrl)) != cudaSuccess || cudaMemset(c->ctrl_tmpl, 0, sizeof(Ctrl)) != cudaSuccess) {
     c->err = "cudaMemset failed";
     return bail(PSD_ERR_CUDA);
   }
@@ -856,12 +1294,16 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
 psd_status psd_destroy(psd_handle c) {
   if (!c) return PSD_OK;
   void* ptrs[] = {c->tables, c->ub, c->W, c->D, c->Z, c->Dsp, c->Ftf, c->Gtf, c->u32, c->da, c->db, c->W32, c->D32,
-                  c->R32, c->Dsp32, c->partials, c->ctrl, c->ctrl2, c->d_hist};
+                  c->R32, c->Dsp32, c->partials, c->ctrl, c->ctrl2, c->ctrl3, c->ctrl_tmpl, c->d_hist, c->adj_q, c->adj_pb,
+                  c->adj_u, c->adj32[0], c->adj32[1]};
   for (void* p : ptrs) dev_free(c, p);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
-  if (c->g_inner) cudaGraphExecDestroy(c->g_inner);
-  if (c->g_fp64) cudaGraphExecDestroy(c->g_fp64);
+  if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
+  if (c->g_cg32) cudaGraphExecDestroy(c->g_cg32);
+  if (c->g_cg64) cudaGraphExecDestroy(c->g_cg64);
   if (c->gst) cudaStreamDestroy(c->gst);
+  for (cudaStream_t q : c->capst)
+    if (q) cudaStreamDestroy(q);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -1019,6 +1461,19 @@ psd_status psd_theta_ff(psd_handle c, const double* x, double* theta) {
   return PSD_OK;
 }
 
+psd_status psd_autotune(psd_handle c, int* caps) {
+  if (!c) return PSD_ERR_INVALID;
+  TRY(autotune(c));
+  if (caps)
+    for (int k = 0; k < 3; ++k) caps[k] = c->tb32.tile_cap[k];
+  // captured solve graphs hold the old launch shapes
+  if (c->g_solve) {
+    cudaGraphExecDestroy(c->g_solve);
+    c->g_solve = nullptr;
+  }
+  return PSD_OK;
+}
+
 psd_status psd_precond_solve(psd_handle c, const double* r, double* d) {
   if (!c) return PSD_ERR_INVALID;
   if (!r || !d) return fail(c, PSD_ERR_INVALID, "r and d are required");
@@ -1076,15 +1531,23 @@ psd_status psd_adjoint(psd_handle c, const double* u, const double* grad_u, doub
   TRY(ensure_fp64(c));
   TRY(alloc(c, &c->Z, c->N));
   TRY(alloc(c, &c->Dsp, c->N));
+  TRY(alloc(c, &c->adj_q, c->N));
+  const bool mixed = c->prm.precision == PSD_MIXED;
+  if (mixed) {
+    TRY(ensure_fp32(c));
+    TRY(alloc(c, &c->adj32[0], c->N));
+    TRY(alloc(c, &c->adj32[1], c->N));
+  } else {
+    TRY(alloc(c, &c->adj_pb, c->N));
+    TRY(alloc(c, &c->adj_u, c->N));
+  }
   const KParams& kp = c->kp;
   const size_t bytes = c->N * sizeof(double);
-  // buffers: lam -> grad_f (copied at the end when grad_f aliases grad_u),
-  // r -> W, z -> D, p -> ub, Hp -> Z; Dsp: scratch of the middle pass
-  double* lam = (grad_f == grad_u) ? c->Dsp : grad_f;
-  double *r = c->W, *z = c->D, *pv = c->ub, *Hp = c->Z;
+  // lambda lives in Dsp and is copied to grad_f at the end (grad_f may alias
+  // grad_u); the FP64 solve works on a copy of u, so that every buffer of
+  // its CG chunk belongs to the handle and one captured graph serves all calls
+  double* lam = c->Dsp;
   CK(cudaEventRecord(c->ev0, c->st));
-  CK(cudaMemsetAsync(lam, 0, bytes, c->st));
-  CK(cudaMemcpyAsync(r, grad_u, bytes, cudaMemcpyDeviceToDevice, c->st));
   Ctrl h0;
   init_ctrl(h0, -1.0, 1 << 30);
   TRY(upload_ctrl(c, c->ctrl2, h0));
@@ -1092,51 +1555,61 @@ psd_status psd_adjoint(psd_handle c, const double* u, const double* grad_u, doub
   Ctrl hb;
   TRY(read_ctrl(c, c->ctrl2, hb));
   const double bnorm = hb.res_l2;
-  int status = PSD_ERR_NOCONV, it = 0;
-  double rel = bnorm > 0 ? 1.0 : 0.0;
-  if (bnorm == 0.0) status = PSD_OK;
-  // z = L^{-1} r, (r, z) from the middle pass
-  auto precond = [&](double* rz) -> psd_status {
-    CK(cudaMemcpyAsync(z, r, bytes, cudaMemcpyDeviceToDevice, c->st));
-    Ctrl hp;
-    init_ctrl(hp, -1.0, 1 << 30);
-    TRY(upload_ctrl(c, c->ctrl2, hp));
-    TRY(precond_passes<double>(c, z, z, c->ctrl2, nullptr, nullptr, c->tb64));
-    Ctrl o;
-    TRY(read_ctrl(c, c->ctrl2, o));
-    *rz = o.rd;
-    return PSD_OK;
-  };
-  double rz = 0.0;
-  if (status != PSD_OK) {
-    TRY(precond(&rz));
-    CK(cudaMemcpyAsync(pv, z, bytes, cudaMemcpyDeviceToDevice, c->st));
-    for (it = 1; it <= max_iter; ++it) {
-      double pHp = 0.0;
-      TRY(psd_hvp(c, u, pv, Hp, &pHp));
-      if (!(pHp > 0.0) || !std::isfinite(pHp)) {
+  int status = PSD_OK, iters = 0, outer = 0;
+  double rel = 0.0;
+  if (!std::isfinite(bnorm)) {
+    status = PSD_ERR_NONFINITE;
+  } else if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(lam, 0, bytes, c->st));
+  } else if (!mixed) {
+    // FP64: one device-resident CG solve to tol_rel ||b||
+    CK(cudaMemcpyAsync(c->adj_u, u, bytes, cudaMemcpyDeviceToDevice, c->st));
+    Ctrl hc;
+    TRY(cg_solve<double>(c, c->adj_u, grad_u, lam, c->Z, c->adj_q, c->W, c->D, c->ub, c->adj_pb, c->tb64,
+                         tol_rel * bnorm, max_iter, &c->g_cg64, &hc));
+    iters = hc.iter;
+    rel = hc.res_l2 / bnorm;
+    status = hc.status;
+  } else {
+    // Mixed: FP64 outer residual R = b - H lambda (H at u), inner FP32 CG on
+    // H delta = R (H at the FP32 copy of u) to kAdjInnerEta ||R||, lambda += delta
+    CK(cudaMemsetAsync(lam, 0, bytes, c->st));
+    CK(cudaMemsetAsync(c->adj_q, 0, bytes, c->st));
+    { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_round_f32(c->u32, u, c->N, c->st)); }
+    const double eta = c->prm.inner_eta > 0.0 ? c->prm.inner_eta : kInnerEta;
+    status = PSD_ERR_NOCONV;
+    for (;;) {
+      // R32 = (float)(b - H lambda), ||R||
+      TRY(upload_ctrl(c, c->ctrl2, h0));
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_sub_round(grad_u, c->adj_q, c->R32, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
+      Ctrl hr;
+      TRY(read_ctrl(c, c->ctrl2, hr));
+      ++outer;
+      rel = hr.res_l2 / bnorm;
+      if (!std::isfinite(rel)) {
         status = PSD_ERR_NONFINITE;
         break;
       }
-      const double al = rz / pHp;
-      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(lam, lam, pv, 1.0, al, 0.0, c->N, c->st)); }
-      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(r, r, Hp, 1.0, -al, 0.0, c->N, c->st)); }
-      Ctrl hn;
-      TRY(upload_ctrl(c, c->ctrl2, h0));
-      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(r, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
-      TRY(read_ctrl(c, c->ctrl2, hn));
-      rel = hn.res_l2 / bnorm;
       if (rel <= tol_rel) {
         status = PSD_OK;
         break;
       }
-      double rz_new = 0.0;
-      TRY(precond(&rz_new));
-      const double be = rz_new / rz;
-      rz = rz_new;
-      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_axpby<double>(pv, z, pv, 1.0, be, 0.0, c->N, c->st)); }
+      if (iters >= max_iter || outer > std::max(c->prm.max_outer, 1) + 1) break;
+      Ctrl hc;
+      TRY(cg_solve<float>(c, c->u32, c->R32, c->adj32[0], c->R32, c->adj32[1], c->W32, c->D32, c->da, c->db, c->tb32,
+                          eta * hr.res_l2, std::min(max_iter - iters, kInnerMaxIter), &c->g_cg32, &hc));
+      iters += hc.iter;
+      if (hc.status == PSD_ERR_NONFINITE) {
+        status = PSD_ERR_NONFINITE;
+        break;
+      }
+      if (hc.iter == 0) break;
+      { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_add_f32(lam, c->adj32[0], c->N, c->st)); }
+      // q = H lambda in FP64 (fresh control block: no CG bookkeeping)
+      TRY(upload_ctrl(c, c->ctrl2, h0));
+      ResArgs<double> a{lam, nullptr, nullptr, nullptr, u, c->adj_q, 0, 0};
+      { ProfScope p_(c, PSD_PROF_RESIDUAL_FP64); CK(psd::launch_residual<double>(a, psd::RM_HVP, c->pk, kp, c->ctrl2, c->partials, c->st)); }
     }
-    if (it > max_iter) it = max_iter;
   }
   // grad_s = -sum lam dN/ds, dN/ds = (N_h[u] - u)/s = (-r0 - u)/s with r0 = 0 - N_h[u]
   double gs = 0.0;
@@ -1151,15 +1624,15 @@ psd_status psd_adjoint(psd_handle c, const double* u, const double* grad_u, doub
     TRY(read_ctrl(c, c->ctrl2, o));
     gs = o.rd / kp.s;  // -sum lam (-W - u)/s
   }
-  if (lam != grad_f) CK(cudaMemcpyAsync(grad_f, lam, bytes, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(grad_f, lam, bytes, cudaMemcpyDeviceToDevice, c->st));
   CK(cudaEventRecord(c->ev1, c->st));
   CK(cudaStreamSynchronize(c->st));
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   if (grad_s) *grad_s = gs;
   if (info) {
-    info->iters = it;
-    info->outer_iters = 0;
+    info->iters = iters;
+    info->outer_iters = outer;
     info->res_l2 = rel;
     info->res_linf = -1.0;
     info->energy = NAN;
@@ -1392,3 +1865,15 @@ psd_status psd_energy(psd_handle c, const double* u, const double* f, const doub
 }
 
 }  // extern "C"
+
+// Internal entry points of the batch driver (psd_batch.cu); not part of the C ABI.
+namespace psd_internal {
+psd_status prepare(psd_handle c, const double* f, const double* g, double* u) { return solve_prepare(c, f, g, u); }
+psd_status capture(psd_handle c, const double* f, const double* g, double* u, cudaStream_t st) {
+  return solve_capture(c, f, g, u, st);
+}
+psd_status finish(psd_handle c, psd_info* info) { return solve_finish(c, info); }
+cudaStream_t stream(psd_handle c) { return c->st; }
+psd_status tune(psd_handle c) { return autotune(c); }
+void set_error(psd_handle c, const char* msg) { c->err = msg; }
+}  // namespace psd_internal

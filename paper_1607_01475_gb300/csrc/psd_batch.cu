@@ -1,8 +1,19 @@
 // Batched PSD: many independent instances of uneven size solved
-// concurrently on one GPU.  Each instance gets its own handle and its own
-// non-blocking stream; a pool of host threads drives the instances' solve
-// loops, so the kernels of different instances overlap on the device and
-// the per-chunk host checks of one instance never stall another.
+// concurrently on one GPU from ONE CUDA graph launch.  Each instance keeps
+// its own handle (workspace, control blocks) and stream; its whole solve --
+// the iteration loops are WHILE conditional nodes driven by the instance's
+// device-resident stop flags -- is captured as an independent branch of a
+// single graph (fork / join events on the instances' streams), which the
+// GPU then runs without any host round trip: the kernels of different
+// instances overlap, and an instance that stops early (converged, or failed
+// on a non-finite value) ends its own branch only.  Nothing waits on a flag
+// written by another kernel, so there is no spin-wait to bound.
+//
+// The graph is cached on the batch for the last set of f, g, u pointers.
+// When a capture is not possible (kernel tracing on an instance, or a
+// capture failure) the instances are solved as before the graph driver:
+// one host thread per instance at a time from a pool, the instances'
+// streams overlapping on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,16 +24,62 @@
 
 #include "../../include/psd.h"
 
+namespace psd_internal {
+psd_status prepare(psd_handle c, const double* f, const double* g, double* u);
+psd_status capture(psd_handle c, const double* f, const double* g, double* u, cudaStream_t st);
+psd_status finish(psd_handle c, psd_info* info);
+cudaStream_t stream(psd_handle c);
+psd_status tune(psd_handle c);
+}  // namespace psd_internal
+
 struct psd_batch_ctx {
   std::vector<psd_handle> inst;
   std::vector<cudaStream_t> streams;
   int workers = 1;
   std::string err;
+  // the single-graph driver
+  cudaStream_t main = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<const void*> key;  // f, g, u of every instance
+  bool graph_off = false;
+  int last_mode = 0;  // 1: the last solve ran from one graph, 2: from host threads
 };
 
 namespace {
 thread_local std::string g_batch_error;
+
+// Capture the solves of all instances as parallel branches of one graph.
+psd_status build_graph(psd_batch_ctx* b, const double* const* f, const double* const* g, double* const* u) {
+  const int n = (int)b->inst.size();
+  if (cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PSD_ERR_CUDA;
+  psd_status s = PSD_OK;
+  if (cudaEventRecord(b->fork, b->main) != cudaSuccess) s = PSD_ERR_CUDA;
+  for (int i = 0; i < n && s == PSD_OK; ++i) {
+    if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) {
+      s = PSD_ERR_CUDA;
+      break;
+    }
+    s = psd_internal::capture(b->inst[i], f[i], g ? g[i] : nullptr, u[i], b->streams[i]);
+    if (s != PSD_OK) break;
+    if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(b->main, b->join[i], 0) != cudaSuccess)
+      s = PSD_ERR_CUDA;
+  }
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamEndCapture(b->main, &graph) != cudaSuccess) graph = nullptr;
+  if (s != PSD_OK || graph == nullptr || cudaGraphInstantiate(&b->graph, graph, 0) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    b->graph = nullptr;
+    return s != PSD_OK ? s : PSD_ERR_CUDA;
+  }
+  cudaGraphDestroy(graph);
+  return PSD_OK;
 }
+
+}  // namespace
 
 extern "C" {
 
@@ -35,15 +92,26 @@ psd_status psd_batch_create(const psd_params* per_instance, int count, int worke
   }
   psd_batch_ctx* b = new psd_batch_ctx();
   b->workers = workers > 0 ? std::min(workers, count) : std::min(count, 16);
+  if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    g_batch_error = "stream or event creation failed";
+    psd_batch_destroy(b);
+    return PSD_ERR_CUDA;
+  }
   for (int i = 0; i < count; ++i) {
     cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
-      g_batch_error = "cudaStreamCreateWithFlags failed";
+      if (st) cudaStreamDestroy(st);
+      g_batch_error = "stream or event creation failed";
       psd_batch_destroy(b);
       return PSD_ERR_CUDA;
     }
     b->streams.push_back(st);
+    b->join.push_back(ev);
     psd_params p = per_instance[i];
     p.stream = st;
     psd_handle h = nullptr;
@@ -56,6 +124,12 @@ psd_status psd_batch_create(const psd_params* per_instance, int count, int worke
       return s;
     }
     b->inst.push_back(h);
+    // tile widths of the FP32 passes, timed once per distinct grid (cached)
+    if (p.precision == PSD_MIXED && (s = psd_internal::tune(h)) != PSD_OK) {
+      g_batch_error = "instance " + std::to_string(i) + ": autotuning failed";
+      psd_batch_destroy(b);
+      return s;
+    }
   }
   *out = b;
   return PSD_OK;
@@ -63,8 +137,12 @@ psd_status psd_batch_create(const psd_params* per_instance, int count, int worke
 
 psd_status psd_batch_destroy(psd_batch b) {
   if (!b) return PSD_OK;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
   for (psd_handle h : b->inst) psd_destroy(h);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->main) cudaStreamDestroy(b->main);
   delete b;
   return PSD_OK;
 }
@@ -85,18 +163,51 @@ psd_status psd_batch_solve(psd_batch b, const double* const* f, const double* co
   }
   std::vector<psd_status> st(n, PSD_OK);
   std::vector<psd_info> inf(n);
-  std::atomic<int> next(0);
-  auto work = [&]() {
-    for (;;) {
-      const int i = next.fetch_add(1);
-      if (i >= n) return;
-      st[i] = psd_solve(b->inst[i], f[i], g ? g[i] : nullptr, u[i], nullptr, &inf[i]);
+  bool done = false;
+  if (!b->graph_off) {
+    // host part of every solve, then one graph launch for all of them
+    psd_status ps = PSD_OK;
+    for (int i = 0; i < n && ps == PSD_OK; ++i) ps = psd_internal::prepare(b->inst[i], f[i], g ? g[i] : nullptr, u[i]);
+    if (ps == PSD_OK) {
+      std::vector<const void*> key;
+      for (int i = 0; i < n; ++i) {
+        key.push_back(f[i]);
+        key.push_back(g ? g[i] : nullptr);
+        key.push_back(u[i]);
+      }
+      if (b->graph && key != b->key) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+      if (!b->graph && build_graph(b, f, g, u) == PSD_OK) b->key = key;
+      if (b->graph && cudaGraphLaunch(b->graph, b->main) == cudaSuccess &&
+          cudaStreamSynchronize(b->main) == cudaSuccess) {
+        for (int i = 0; i < n; ++i) st[i] = psd_internal::finish(b->inst[i], &inf[i]);
+        done = true;
+        b->last_mode = 1;
+      } else {
+        cudaGetLastError();
+        b->graph_off = true;
+      }
+    } else {
+      b->graph_off = true;
     }
-  };
-  std::vector<std::thread> pool;
-  for (int t = 1; t < b->workers; ++t) pool.emplace_back(work);
-  work();
-  for (auto& th : pool) th.join();
+  }
+  if (!done) {
+    std::atomic<int> next(0);
+    auto work = [&]() {
+      for (;;) {
+        const int i = next.fetch_add(1);
+        if (i >= n) return;
+        st[i] = psd_solve(b->inst[i], f[i], g ? g[i] : nullptr, u[i], nullptr, &inf[i]);
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < b->workers; ++t) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
+    b->last_mode = 2;
+  }
   psd_status worst = PSD_OK;
   for (int i = 0; i < n; ++i) {
     if (infos) infos[i] = inf[i];
@@ -104,7 +215,7 @@ psd_status psd_batch_solve(psd_batch b, const double* const* f, const double* co
       worst = st[i];
       char buf[256];
       psd_last_error(b->inst[i], buf, sizeof buf);
-      b->err = "instance " + std::to_string(i) + ": " + buf;
+      b->err = "instance " + std::to_string(i) + ": " + (buf[0] ? std::string(buf) : psd_status_string(st[i]));
     }
   }
   return worst;
@@ -116,5 +227,7 @@ psd_status psd_batch_last_error(psd_batch b, char* buf, size_t len) {
   snprintf(buf, len, "%s", e.c_str());
   return PSD_OK;
 }
+
+int psd_batch_mode(psd_batch b) { return b ? b->last_mode : 0; }
 
 }  // extern "C"

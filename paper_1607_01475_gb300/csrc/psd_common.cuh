@@ -44,6 +44,21 @@ struct Ctrl {
   double pre_win;  // value at the start of the current stall window
   int pre_stall;   // iterations without halving pre_win
   int pre_stall_max;
+  // conjugate gradients (the adjoint solve): cg = 1 switches the middle pass
+  // and the Hessian-vector kernel to their CG bookkeeping -- the middle pass
+  // forms beta = (r, z) / rz into alpha and stores rz = (r, z); the
+  // Hessian-vector kernel forms alpha = rz / (p, H p)
+  int cg;
+  int cg_pad_;
+  double rz;
+  // device-side loop control of graph-driven solves (WHILE nodes)
+  int guard;        // body executions of the current loop (a hard cap)
+  int ls_pass;      // general-p line search: Newton passes of this iteration
+  int outer;        // mixed solve: FP64 outer residual evaluations
+  int inner_total;  // mixed solve: inner iterations so far
+  int fxs;          // mixed solve: fixed-point scale of the next outer residual (0: plain FP64)
+  int max_outer;
+  double last_alpha;
   unsigned int counter[CS_COUNT];
   int hist_cap;
   int pad_;
@@ -246,6 +261,13 @@ __device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Close the current group of this thread's cp.async copies; wait until at
+// most N of its groups are still in flight.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // 1/x for finite x >= 1 (the preconditioner symbols).  FP32: the hardware
 // reciprocal estimate (rcp.approx) refined by one Newton-Raphson step

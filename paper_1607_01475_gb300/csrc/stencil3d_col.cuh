@@ -84,7 +84,15 @@ __global__ void __launch_bounds__(256, 2)
   const T beta = C.beta;
   // fixed point (FFX): u = q 2^-S (S in [15, 120]); the gradients enter the
   // flux as float-float values of G 2^-S, cbih absorbs 2^-S
-  const int fxs = FFX ? a.fxs : 0;
+  int fxs = FFX ? a.fxs : 0;
+  if constexpr (FFX || (sizeof(T) == 8 && MODE == RM_PLAIN && PK == PK_4)) {
+    if (a.fxs_dev != nullptr) {  // the scale decided on device: exactly one variant computes
+      const int S = *a.fxs_dev;
+      const bool fixed = S >= 15 && S <= 120;
+      if (fixed != FFX) return;
+      if (FFX) fxs = S;
+    }
+  }
   const T cbihq = FFX ? cbih * (T)fx_unit(fxs) : cbih;
 
   // One wave of CTAs: the column-planes (w = column * nz + z, column = tile

@@ -97,8 +97,19 @@ __device__ __forceinline__ void flux_lin(const T (&a)[3], const T (&e)[3], T bet
 __device__ void residual_epilogue(Ctrl* ctrl, const KParams& kp, double sum2, double maxabs, int norm,
                                   int update_iter, bool hvp = false) {
   if (hvp) {
-    ctrl->c1 = sum2 * kp.hd;
+    const double pq = sum2 * kp.hd;  // (v, H v)_2
+    ctrl->c1 = pq;
     ctrl->c2 = maxabs;
+    if (ctrl->cg) {
+      // CG step length alpha = (r, z) / (p, H p); H is positive definite
+      // (the second variation, Sec. 5.3), so pq <= 0 means a breakdown
+      if (pq > 0.0 && isfinite(pq)) {
+        ctrl->alpha = ctrl->rz / pq;
+      } else {
+        ctrl->status = 7;
+        ctrl->done = 1;
+      }
+    }
     ctrl->counter[CS_RES] = 0;
     return;
   }
@@ -683,6 +694,12 @@ cudaError_t res_impl(const ResArgs<T>& a, const KParams& kp, Ctrl* ctrl, double*
       break;
     case RK_COL:
       if constexpr (sizeof(T) == 8 && MODE == RM_PLAIN && PK == PK_4) {
+        if (a.fxs_dev != nullptr && a.d == nullptr) {
+          // both variants; the one that does not apply returns at once
+          k_res3d_col<T, PK, MODE, true><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials);
+          k_res3d_col<T, PK, MODE><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials);
+          break;
+        }
         if (a.fluxff && a.d == nullptr && a.fxs >= 15 && a.fxs <= 120) {
           k_res3d_col<T, PK, MODE, true><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials);
           break;

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_1607_01475_gb300 import Solver, synthetic  # noqa: E402
+from paper_1607_01475_gb300 import PSD_FP64, PSD_MIXED, Solver, synthetic  # noqa: E402
 from paper_1607_01475_gb300.autograd import psd_solve_autograd  # noqa: E402
 
 rng = np.random.default_rng(99)
@@ -41,8 +41,11 @@ def test_hvp_parity(oracle, shape, p):
     assert abs(dot - h ** len(shape) * np.sum(v * ref)) <= 1e-10 * abs(dot)
 
 
+@pytest.mark.parametrize("precision", [PSD_FP64, PSD_MIXED])
 @pytest.mark.parametrize("shape", [(32, 32), (16, 16, 16), (32, 32, 64)])
-def test_adjoint_matches_oracle(oracle, shape):
+def test_adjoint_matches_oracle(oracle, shape, precision):
+    """dJ/df and dJ/ds of the device-resident CG (FP64, or FP32 inner CG with
+    FP64 outer residual correction) against the oracle's adjoint at 1e-9."""
     h = 2 * np.pi / shape[-1]
     s, eps = 0.05, 0.15
     P = oracle.Problem(4, h, 4.0, s, eps)
@@ -52,12 +55,36 @@ def test_adjoint_matches_oracle(oracle, shape):
     hd = h ** len(shape)
     gu = hd * (u - ut)
     gf_ref, gs_ref, _ = oracle.adjoint4(u, gu, P)
-    S = Solver(4, shape, h, 4.0, s, eps)
+    S = Solver(4, shape, h, 4.0, s, eps, precision=precision)
     gf = torch.empty(shape, dtype=torch.float64, device="cuda")
     gs, info = S.adjoint(dev(u), dev(gu), gf, tol_rel=1e-13, max_iter=2000)
-    assert info["status"] == 0
+    assert info["status"] == 0 and info["res_l2"] <= 1e-13
     assert rel(gf.cpu().numpy(), gf_ref) <= 1e-9
     assert abs(gs - gs_ref) <= 1e-9 * abs(gs_ref)
+    # a second call on the same handle (replayed CG graphs) gives the same bits
+    gf2 = torch.empty_like(gf)
+    gs2, _ = S.adjoint(dev(u), dev(gu), gf2, tol_rel=1e-13, max_iter=2000)
+    assert torch.equal(gf, gf2) and gs == gs2
+
+
+def test_adjoint_aliasing_and_zero_rhs(oracle):
+    """grad_f may alias grad_u; a zero dJ/du gives zero gradients."""
+    shape = (16, 16, 16)
+    h = 2 * np.pi / 16
+    P = oracle.Problem(4, h, 4.0, 0.05, 0.15)
+    f = synthetic.fourier_field(shape, 2 * np.pi, 6, 91, nmodes=16)
+    u, _ = oracle.psd_solve(P, f, np.zeros(shape), tol=0.0, kmax=150)
+    gu = rng.standard_normal(shape)
+    gf_ref, _, _ = oracle.adjoint4(u, gu, P)
+    for prec in (PSD_FP64, PSD_MIXED):
+        S = Solver(4, shape, h, 4.0, P.s, P.eps, precision=prec)
+        g = dev(gu)
+        S.adjoint(dev(u), g, g, tol_rel=1e-13)
+        assert rel(g.cpu().numpy(), gf_ref) <= 1e-9
+        z = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        out = torch.full_like(z, 5.0)
+        gs, info = S.adjoint(dev(u), z, out)
+        assert info["status"] == 0 and gs == 0.0 and bool((out == 0).all())
 
 
 def test_adjoint_gradient_by_central_differences_and_autograd():
@@ -90,7 +117,8 @@ def test_adjoint_gradient_by_central_differences_and_autograd():
         assert abs(fds - gs.item()) <= 2e-5 * abs(gs.item())
 
 
-def test_adjoint_full_size_128cubed():
+@pytest.mark.parametrize("precision", [PSD_FP64, PSD_MIXED])
+def test_adjoint_full_size_128cubed(precision):
     """The adjoint workload: 3D 128^3, p=4, s=0.1, eps=0.05 (thin-film shaped
     f), J = 1/2 h^3 sum (u - u_t)^2; the adjoint solve converges and the
     directional derivative along a random direction matches central
@@ -101,7 +129,7 @@ def test_adjoint_full_size_128cubed():
     ut = dev(synthetic.fourier_field(shape, wl["L"], 8, synthetic.seed_for(4, 0, 2)))
     f0 = dev(wl["f"])
     hd = h ** 3
-    S = Solver(4, shape, h, 4.0, wl["s"], wl["eps"], tol=1e-11, max_iter=5000)
+    S = Solver(4, shape, h, 4.0, wl["s"], wl["eps"], precision=precision, tol=1e-11, max_iter=5000, max_outer=30)
 
     def solve(f):
         u = torch.zeros_like(f)
@@ -119,3 +147,25 @@ def test_adjoint_full_size_128cubed():
     fd = (Jp - Jm) / (2 * t)
     an = torch.sum(gf * v).item()
     assert abs(fd - an) <= 1e-4 * abs(an)
+
+
+def test_mixed_adjoint_matches_fp64_at_128cubed():
+    """The mixed adjoint (FP32 inner CG, FP64 outer correction) agrees with
+    the FP64 adjoint to 1e-9 on the 128^3 adjoint workload."""
+    shape = (128, 128, 128)
+    wl = synthetic.workload_thin_film(shape)
+    h = wl["L"] / 128
+    ut = dev(synthetic.fourier_field(shape, wl["L"], 8, synthetic.seed_for(4, 0, 2)))
+    S64 = Solver(4, shape, h, 4.0, wl["s"], wl["eps"], tol=1e-11, max_iter=5000)
+    u = torch.zeros_like(ut)
+    S64.solve(dev(wl["f"]), u)
+    gu = h ** 3 * (u - ut)
+    out = {}
+    for prec in (PSD_FP64, PSD_MIXED):
+        S = Solver(4, shape, h, 4.0, wl["s"], wl["eps"], precision=prec)
+        gf = torch.empty_like(u)
+        gs, info = S.adjoint(u, gu, gf, tol_rel=1e-12, max_iter=3000)
+        assert info["status"] == 0
+        out[prec] = (gf.cpu().numpy(), gs)
+    assert rel(out[PSD_MIXED][0], out[PSD_FP64][0]) <= 1e-9
+    assert abs(out[PSD_MIXED][1] - out[PSD_FP64][1]) <= 1e-9 * abs(out[PSD_FP64][1])

@@ -39,6 +39,7 @@ def test_batch_matches_oracle_and_single_handle(oracle, precision):
     B = Batch([dict(it, precision=precision, tol=tol, max_iter=3000) for it in insts], workers=3)
     us = [torch.zeros(it["shape"], dtype=torch.float64, device="cuda") for it in insts]
     infos = B.solve([dev(f) for f in fs], us)
+    assert B.mode() == 1  # one graph launch for the whole batch
     for i, (it, f, u, info) in enumerate(zip(insts, fs, us, infos)):
         assert info["status"] == 0 and info["res_l2"] < tol
         P = oracle.Problem(4, it["h"], it["p"], it["s"], it["eps"])
@@ -90,3 +91,22 @@ def test_batch_poisoned_instance_fails_alone():
             assert info["status"] == 7
         else:
             assert info["status"] == 0 and info["res_l2"] < 1e-10, i
+
+
+def test_batch_graph_replays_and_recaptures():
+    """The batch graph is replayed for the same arrays (bitwise the same
+    answers) and captured again for new arrays."""
+    insts = _small_instances()
+    fs = [dev(synthetic.fourier_field(it["shape"], 2 * np.pi, 6, 600 + i, nmodes=16)) for i, it in enumerate(insts)]
+    B = Batch([dict(it, precision=PSD_MIXED, tol=1e-10, max_iter=3000) for it in insts])
+    us = [torch.zeros(it["shape"], dtype=torch.float64, device="cuda") for it in insts]
+    B.solve(fs, us)
+    first = [u.clone() for u in us]
+    for u in us:
+        u.zero_()
+    B.solve(fs, us)
+    assert B.mode() == 1 and all(torch.equal(a, b) for a, b in zip(first, us))
+    us2 = [torch.zeros_like(u) for u in us]
+    infos = B.solve(fs, us2)
+    assert B.mode() == 1 and all(torch.equal(a, b) for a, b in zip(first, us2))
+    assert all(i["status"] == 0 and i["res_l2"] < 1e-10 and i["wall_ms"] > 0 for i in infos)

@@ -267,19 +267,29 @@ def test_converged_parity_fp64(oracle, shape, order, p):
 @pytest.mark.parametrize("order,p", [(4, 4.0), (6, 4.0), (4, 3.0), (4, 6.0), (6, 6.0)])
 def test_mixed_precision_parity(oracle, shape, order, p):
     """FP32 inner PSD + outer FP64 residual correction reaches the FP64
-    solution to 1e-9 relative."""
+    solution to 1e-9 relative.  For p = 6 the oracle's PSD needs thousands
+    of iterations to reach its FP64 floor, so the answer is checked by the
+    oracle's own residual instead: E_h is strongly convex (its second
+    variation is at least (xi, xi)_2 for order 4 and s lambda (xi, xi)_2 on
+    the mean-zero space for order 6), so ||u - u*||_2 <= ||r||_2 / m."""
     P, h = _problem(oracle, order, shape, p, s=0.05, eps=0.15, lam=1.0)
     f = smooth_random(shape, seed=7)
     g = smooth_random(shape, seed=9) if order == 6 else None
     u0 = np.zeros(shape) if order == 4 else np.full(shape, g.mean())
-    u_ref, _ = oracle.psd_solve(P, f, u0, g=g, tol=0.0, kmax=150)
     S = Solver(order, shape, h, p, P.s, P.eps, P.lam, precision=PSD_MIXED, tol=1e-11, max_iter=2000,
                max_outer=30)
     u = dev(u0)
     info = S.solve(dev(f), u, None if g is None else dev(g))
     assert info["status"] == 0
     assert info["res_l2"] < 1e-11
-    assert rel(host(u), u_ref) <= 1e-9
+    if p != 6.0:
+        u_ref, _ = oracle.psd_solve(P, f, u0, g=g, tol=0.0, kmax=150)
+        assert rel(host(u), u_ref) <= 1e-9
+    else:
+        r = oracle.residual4(host(u), f, P) if order == 4 else oracle.residual6(host(u), f, g, P)
+        assert oracle.norm2(r, h) < 1.05e-11
+        if order == 6:
+            assert abs(host(u).mean() - g.mean()) < 1e-13
 
 
 # ---------------------------------------------------------------- edges
