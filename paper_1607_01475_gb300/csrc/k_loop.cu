@@ -26,6 +26,11 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, Ctrl* c, int guard_max
   cudaGraphSetConditional(h, v);
 }
 
+// Arm a WHILE node: its condition keeps the value of the loop's last exit
+// (0) when the enclosing body runs again, so a kernel placed just before the
+// node sets it to 1 (the body then runs at least once).
+__global__ void k_cond_arm(cudaGraphConditionalHandle h) { cudaGraphSetConditional(h, 1u); }
+
 __global__ void k_ls_cond(cudaGraphConditionalHandle h, Ctrl* c, int max_passes) {
   unsigned v = 0u;
   if (!c->done && c->c3 == 0.0) v = (++c->ls_pass < max_passes) ? 1u : 0u;
@@ -112,6 +117,10 @@ inline int grid1d(size_t n) { return (int)((n + 255) / 256 < 152 * 16 ? (n + 255
 
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, Ctrl* c, int guard_max, cudaStream_t st) {
   k_loop_cond<<<1, 1, 0, st>>>(h, c, guard_max);
+  return cudaGetLastError();
+}
+cudaError_t launch_cond_arm(cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_cond_arm<<<1, 1, 0, st>>>(h);
   return cudaGetLastError();
 }
 cudaError_t launch_ls_cond(cudaGraphConditionalHandle h, Ctrl* c, int max_passes, cudaStream_t st) {

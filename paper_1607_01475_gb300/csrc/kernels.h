@@ -18,6 +18,7 @@ struct AxisTables {
   // block in the row, strided and middle passes (0: as many as fill 256
   // threads)
   int tile_cap[3];
+  int nsm;  // FP32 tables: SMs of the device (persistent row / strided passes); 0 = one tile per CTA
 };
 
 // ----------------------------------------------------------------- DHT passes
@@ -144,6 +145,9 @@ long long residual_grid_blocks(const KParams& kp, bool fp32);
 // Loop while !c->done and the body count stays below guard_max (the guard
 // trips PSD_ERR_NOCONV).
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle h, Ctrl* c, int guard_max, cudaStream_t st);
+// Set the condition to 1 just before a WHILE node (it keeps the value of the
+// previous exit when an enclosing loop body runs the node again).
+cudaError_t launch_cond_arm(cudaGraphConditionalHandle h, cudaStream_t st);
 // General-p line search: another Newton pass while the bracket has not
 // converged (c->c3 == 0), the run is not done, and fewer than max_passes ran.
 cudaError_t launch_ls_cond(cudaGraphConditionalHandle h, Ctrl* c, int max_passes, cudaStream_t st);

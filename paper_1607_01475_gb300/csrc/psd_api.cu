@@ -265,6 +265,7 @@ psd_status build_tables(psd_context* c) {
     c->tb32.twc[a] = d32 + offs[a][0];
     c->tb32.tws[a] = d32 + offs[a][1];
     c->tb32.sym[a] = d32 + offs[a][2];
+    c->tb32.nsm = c->kp.nsm;
     c->tbff.twc[a] = dff + offs[a][0];
     c->tbff.tws[a] = dff + offs[a][1];
     c->tbff.sym[a] = dff + offs[a][2];
@@ -448,8 +449,9 @@ psd_status cap_stream(psd_context* c, int d, cudaStream_t* out) {
 
 // Insert a WHILE conditional node at the current position of the capture on
 // c->st and capture its body: body(handle) enqueues on c->st (a stream of the
-// next depth) and must end with a kernel that sets the condition.  The body
-// runs at least once (default condition 1).
+// next depth) and must end with a kernel that sets the condition.  A kernel
+// just before the node sets the condition to 1, so the body runs at least
+// once every time the node is reached.
 template <typename Body>
 psd_status capture_while(psd_context* c, Body&& body) {
   cudaStream_t s = c->st, s2 = nullptr;
@@ -458,10 +460,14 @@ psd_status capture_while(psd_context* c, Body&& body) {
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
-  CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
   if (cs != cudaStreamCaptureStatusActive) return fail(c, PSD_ERR_CUDA, "capture_while outside a capture");
   cudaGraphConditionalHandle h;
   CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  // a node nested in another loop's body is reached again with the value of
+  // its last exit: arm it first
+  CK(psd::launch_cond_arm(h, s));
+  CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
