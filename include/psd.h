@@ -346,8 +346,14 @@ psd_status psd_batch_solve(psd_batch b, const double* const* f,
                            psd_info* infos);
 psd_status psd_batch_destroy(psd_batch b);
 psd_status psd_batch_last_error(psd_batch b, char* buf, size_t len);
-/* How the last psd_batch_solve ran: 1 = one graph launch, 2 = host threads
- * (0 = none yet or b NULL).                                                */
+/* Schedule of psd_batch_solve: 1 = one graph launch with a branch per
+ * instance; 2 = every instance's own solve graph launched on its own stream
+ * from the calling thread (no host round trip inside a solve); 3 = a pool
+ * of host threads, one solve per thread at a time; 0 = the default (1).
+ * PSD_ERR_INVALID for another value.  psd_batch_mode returns the schedule
+ * the last solve used (a graph capture that fails falls back to 2 or 3;
+ * 0 = no solve yet or b NULL).                                             */
+psd_status psd_batch_set_mode(psd_batch b, int mode);
 int psd_batch_mode(psd_batch b);
 
 /* Text of the last error on this handle (or of the last psd_create failure

@@ -114,6 +114,8 @@ def load_library(build_if_missing=True):
     lib.psd_batch_last_error.argtypes = [H, ctypes.c_char_p, ctypes.c_size_t]
     lib.psd_batch_mode.argtypes = [H]
     lib.psd_batch_mode.restype = ctypes.c_int
+    lib.psd_batch_set_mode.argtypes = [H, ctypes.c_int]
+    lib.psd_batch_set_mode.restype = ctypes.c_int
     lib.psd_residual_noalloc.argtypes = [ctypes.POINTER(PSDParams), D, D, D, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     lib.psd_noalloc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
@@ -351,8 +353,14 @@ class Batch:
         return [i.as_dict() for i in infos]
 
     def mode(self):
-        """1: the last solve ran from one graph launch; 2: from host threads."""
+        """Schedule of the last solve: 1 one graph, 2 per-instance graphs, 3 host threads."""
         return load_library().psd_batch_mode(self.handle)
+
+    def set_mode(self, mode):
+        """0 default, 1 one graph, 2 per-instance graphs on their streams, 3 host threads."""
+        st = load_library().psd_batch_set_mode(self.handle, int(mode))
+        if st != 0:
+            raise PSDError(st, "invalid batch mode")
 
     def close(self):
         if self.handle:

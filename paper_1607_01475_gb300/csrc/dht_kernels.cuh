@@ -140,70 +140,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Persistent FP32 row pass (the inner iteration): a grid of 2 CTAs per SM
-// loops over groups of 2 * pairs rows; every thread cp.async-prefetches its
-// own elements of the next group (staged [element][thread], conflict free)
-// while the current group is transformed.
-template <int N, int RM>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_rows_pf(const float* src, float* dst, int nrows, int ntiles, float scale, const int* done,
-              const float* __restrict__ twc, const float* __restrict__ tws) {
-  using F = LineFFT<float, N, RM>;
-  if (done != nullptr && *done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sm = reinterpret_cast<float*>(smem_raw);
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int pairs = nthr / F::TS;
-  const int p = tid / F::TS, j = tid - p * F::TS;
-  constexpr int LS = line_stride_words<float, N, RM, true>();
-  float* sr = sm + (size_t)p * 2 * LS;
-  float* si = sr + LS;
-  float* stage = sm + align16((size_t)pairs * 2 * LS * sizeof(float)) / sizeof(float);
-  const unsigned stage_elems = 2u * F::R * nthr;
-  auto fetch = [&](int t, int buf) {
-    const int row0 = 2 * (t * pairs + p);
-    if (row0 >= nrows) return;
-    const float* s0 = src + (unsigned)row0 * N;
-    float* st = stage + (unsigned)buf * stage_elems;
-#pragma unroll
-    for (int q = 0; q < F::R; ++q) {
-      cp_async_4(st + (2 * q) * nthr + tid, s0 + j + q * F::TS);
-      cp_async_4(st + (2 * q + 1) * nthr + tid, s0 + N + j + q * F::TS);
-    }
-  };
-  if ((int)blockIdx.x < ntiles) fetch(blockIdx.x, 0);
-  cp_async_commit();
-  int it = 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-    if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x, (it + 1) & 1);
-    cp_async_commit();
-    cp_async_wait_group<1>();
-    const int row0 = 2 * (t * pairs + p);
-    const bool valid = row0 < nrows;
-    const float* st = stage + (unsigned)(it & 1) * stage_elems;
-    float vr[F::R], vi[F::R];
-#pragma unroll
-    for (int q = 0; q < F::R; ++q) {
-      vr[q] = valid ? st[(2 * q) * nthr + tid] : 0.0f;
-      vi[q] = valid ? st[(2 * q + 1) * nthr + tid] : 0.0f;
-    }
-    F::run(vr, vi, j, sr, si, twc, tws);
-    if (valid) {
-      float* d0 = dst + (unsigned)row0 * N;
-#pragma unroll
-      for (int q = 0; q < F::R; ++q) {
-        const int k = j + q * F::TS;
-        float h1, h2;
-        dht_split(sr, si, k, N, h1, h2);
-        d0[k] = h1 * scale;
-        d0[N + k] = h2 * scale;
-      }
-    }
-    __syncthreads();  // the line buffers are rewritten by the next group
-  }
-  cp_async_wait_all();
-}
-
 // ------------------------------------------------------ strided lines (y, z)
 // Block: `pairs` pairs of adjacent x-columns (x, x+1) packed as re/im, lines
 // along the strided axis; thread (p, j) = (tid % pairs, tid / pairs) so that a
@@ -242,64 +178,6 @@ __global__ void __launch_bounds__(kThreads)
     o.y = to_storage<S>(scaled(h2, scale));
     *reinterpret_cast<V*>(data + base + (size_t)k * line_stride) = o;
   }
-}
-
-// Persistent FP32 strided pass (the inner iteration): tiles of 2 * pairs
-// x-columns at one outer index, looped over by a grid of 2 CTAs per SM with
-// the next tile's elements cp.async-prefetched by their own threads.
-template <int N, int RM>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_cols_pf(float* data, unsigned line_stride, unsigned outer_stride, int ntx, int ntiles, float scale,
-              const int* done, const float* __restrict__ twc, const float* __restrict__ tws) {
-  using F = LineFFT<float, N, RM>;
-  if (done != nullptr && *done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sm = reinterpret_cast<float*>(smem_raw);
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int pairs = nthr / F::TS;
-  const int p = tid % pairs, j = tid / pairs;
-  constexpr int LS = line_stride_words<float, N, RM, false>();
-  float* sr = sm + (size_t)p * 2 * LS;
-  float* si = sr + LS;
-  float2* stage = reinterpret_cast<float2*>(smem_raw + align16((size_t)pairs * 2 * LS * sizeof(float)));
-  const unsigned stage_elems = (unsigned)F::R * nthr;
-  auto base_of = [&](int t) {
-    const int xb = t % ntx, yo = t / ntx;
-    return (unsigned)yo * outer_stride + (unsigned)(xb * 2 * pairs + 2 * p);
-  };
-  auto fetch = [&](int t, int buf) {
-    const unsigned b = base_of(t);
-    float2* st = stage + (unsigned)buf * stage_elems;
-#pragma unroll
-    for (int q = 0; q < F::R; ++q) cp_async_8(st + q * nthr + tid, data + (b + (unsigned)(j + q * F::TS) * line_stride));
-  };
-  if ((int)blockIdx.x < ntiles) fetch(blockIdx.x, 0);
-  cp_async_commit();
-  int it = 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-    if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x, (it + 1) & 1);
-    cp_async_commit();
-    cp_async_wait_group<1>();
-    const float2* st = stage + (unsigned)(it & 1) * stage_elems;
-    float vr[F::R], vi[F::R];
-#pragma unroll
-    for (int q = 0; q < F::R; ++q) {
-      const float2 v = st[q * nthr + tid];
-      vr[q] = v.x;
-      vi[q] = v.y;
-    }
-    F::run(vr, vi, j, sr, si, twc, tws);
-    const unsigned b = base_of(t);
-#pragma unroll
-    for (int q = 0; q < F::R; ++q) {
-      const int k = j + q * F::TS;
-      float h1, h2;
-      dht_split(sr, si, k, N, h1, h2);
-      *reinterpret_cast<float2*>(data + (b + (unsigned)k * line_stride)) = make_float2(h1 * scale, h2 * scale);
-    }
-    __syncthreads();  // the line buffers are rewritten by the next tile
-  }
-  cp_async_wait_all();
 }
 
 // ------------------------------------ last axis, float-float, fused epilogue
@@ -752,41 +630,23 @@ int pick_pairs(int avail_pairs, int cap = 0) {
 
 template <typename S, typename T, int N, typename SI = S>
 cudaError_t rows_impl(const SI* src, S* dst, int nrows, T scale, const int* done, const T* twc,
-                      const T* tws, cudaStream_t st, int cap = 0, int nsm = 0) {
+                      const T* tws, cudaStream_t st, int cap = 0) {
   constexpr int RM = radix_pass<T>();
   using F = LineFFT<T, N, RM>;
   const int pairs = pick_pairs<T, N, RM, true>(1 << 30, cap);
   const int rows_per_block = 2 * pairs;
-  const int ntiles = (nrows + rows_per_block - 1) / rows_per_block;
-  if constexpr (std::is_same<S, float>::value && std::is_same<T, float>::value && std::is_same<SI, float>::value) {
-    if (nsm > 0) {
-      const size_t sm = align16(pairs * pair_smem<T, N, RM, true>()) + 2 * (size_t)2 * F::R * pairs * F::TS * sizeof(float);
-      const int grid = std::min(ntiles, 2 * nsm);
-      k_rows_pf<N, RM><<<grid, pairs * F::TS, sm, st>>>(src, dst, nrows, ntiles, scale, done, twc, tws);
-      return cudaGetLastError();
-    }
-  }
-  k_dht_rows<S, T, N, RM, SI><<<ntiles, pairs * F::TS, pairs * pair_smem<T, N, RM, true>(), st>>>(
+  const int grid = (nrows + rows_per_block - 1) / rows_per_block;
+  k_dht_rows<S, T, N, RM, SI><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, true>(), st>>>(
       src, dst, nrows, scale, done, twc, tws);
   return cudaGetLastError();
 }
 
 template <typename S, typename T, int N>
 cudaError_t cols_impl(S* data, int nx, int nouter, size_t line_stride, size_t outer_stride, T scale,
-                      const int* done, const T* twc, const T* tws, cudaStream_t st, int cap = 0, int nsm = 0) {
+                      const int* done, const T* twc, const T* tws, cudaStream_t st, int cap = 0) {
   constexpr int RM = radix_pass<T>();
   using F = LineFFT<T, N, RM>;
   const int pairs = pick_pairs<T, N, RM, false>(nx / 2, cap);
-  if constexpr (std::is_same<S, float>::value && std::is_same<T, float>::value) {
-    if (nsm > 0) {
-      const int ntx = nx / (2 * pairs), ntiles = ntx * nouter;
-      const size_t sm = align16(pairs * pair_smem<T, N, RM, false>()) + 2 * (size_t)F::R * pairs * F::TS * sizeof(float2);
-      const int grid = std::min(ntiles, 2 * nsm);
-      k_cols_pf<N, RM><<<grid, pairs * F::TS, sm, st>>>(data, (unsigned)line_stride, (unsigned)outer_stride, ntx, ntiles,
-                                                        scale, done, twc, tws);
-      return cudaGetLastError();
-    }
-  }
   dim3 grid(nx / (2 * pairs), nouter);
   k_dht_cols<S, T, N, RM><<<grid, pairs * F::TS, pairs * pair_smem<T, N, RM, false>(), st>>>(
       data, line_stride, outer_stride, scale, done, twc, tws);
@@ -850,10 +710,6 @@ void set_attrs_T() {
   cudaFuncSetAttribute(k_dht_rows<T, T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   cudaFuncSetAttribute(k_dht_cols<T, T, N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   constexpr bool PST = sizeof(T) == 4;
-  if constexpr (PST) {
-    cudaFuncSetAttribute(k_rows_pf<N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPre);
-    cudaFuncSetAttribute(k_cols_pf<N, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPre);
-  }
   cudaFuncSetAttribute(k_mid<T, N, 4, RD, PST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPre);
   cudaFuncSetAttribute(k_mid<T, N, 6, RD, PST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmemPre);
 }
@@ -877,8 +733,7 @@ void set_attrs_T() {
 template <typename T>
 cudaError_t launch_dht_rows(const T* src, T* dst, int nx, int nrows, T scale, const int* done,
                             const AxisTables<T>& tb, cudaStream_t st) {
-  PSD_DISPATCH_N(nx, (rows_impl<T, T, NN>(src, dst, nrows, scale, done, tb.twc[0], tb.tws[0], st, tb.tile_cap[0],
-                                          tb.nsm)));
+  PSD_DISPATCH_N(nx, (rows_impl<T, T, NN>(src, dst, nrows, scale, done, tb.twc[0], tb.tws[0], st, tb.tile_cap[0])));
 }
 
 template <typename T>
@@ -897,7 +752,7 @@ cudaError_t launch_dht_cols(T* data, const KParams& kp, int ax, T scale, const i
     nouter = kp.ny;
   }
   PSD_DISPATCH_N(n, (cols_impl<T, T, NN>(data, kp.nx, nouter, line_stride, outer_stride, scale, done,
-                                         tb.twc[ax], tb.tws[ax], st, tb.tile_cap[1], tb.nsm)));
+                                         tb.twc[ax], tb.tws[ax], st, tb.tile_cap[1])));
 }
 
 template <typename T>

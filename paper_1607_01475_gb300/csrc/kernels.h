@@ -18,7 +18,6 @@ struct AxisTables {
   // block in the row, strided and middle passes (0: as many as fill 256
   // threads)
   int tile_cap[3];
-  int nsm;  // FP32 tables: SMs of the device (persistent row / strided passes); 0 = one tile per CTA
 };
 
 // ----------------------------------------------------------------- DHT passes

@@ -88,7 +88,8 @@ struct psd_context {
   Ctrl* ctrl2 = nullptr;  // auxiliary reductions (outer residual, norms)
   Ctrl* ctrl3 = nullptr;  // mixed solve: outer-loop state of the captured solve
   Ctrl* ctrl_tmpl = nullptr;  // mixed solve: control block of a fresh inner solve
-  Ctrl* h_ctrl = nullptr; // pinned host mirror
+  Ctrl* h_ctrl = nullptr; // pinned host mirror: [0] synchronous transfers, [1..3] staging of
+                          // asynchronous uploads (a batch's host part)
 
   double* d_hist = nullptr;
   double* user_alpha = nullptr;
@@ -265,7 +266,6 @@ psd_status build_tables(psd_context* c) {
     c->tb32.twc[a] = d32 + offs[a][0];
     c->tb32.tws[a] = d32 + offs[a][1];
     c->tb32.sym[a] = d32 + offs[a][2];
-    c->tb32.nsm = c->kp.nsm;
     c->tbff.twc[a] = dff + offs[a][0];
     c->tbff.tws[a] = dff + offs[a][1];
     c->tbff.sym[a] = dff + offs[a][2];
@@ -371,6 +371,14 @@ psd_status upload_ctrl(psd_context* c, Ctrl* dst, const Ctrl& h) {
   *c->h_ctrl = h;
   CK(cudaMemcpyAsync(dst, c->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
+  return PSD_OK;
+}
+
+// Upload without waiting, from staging slot `slot` (1..3) of the pinned
+// mirror; the slot must not be reused before the copy has run.
+psd_status upload_ctrl_async(psd_context* c, Ctrl* dst, const Ctrl& h, int slot) {
+  c->h_ctrl[slot] = h;
+  CK(cudaMemcpyAsync(dst, c->h_ctrl + slot, sizeof(Ctrl), cudaMemcpyHostToDevice, c->st));
   return PSD_OK;
 }
 
@@ -1067,6 +1075,8 @@ psd_status autotune(psd_context* c) {
 // ------------------------------------------------ batch (internal hooks)
 // The host part of a solve before its graph work: control blocks uploaded
 // (and, order 6 mixed, the mean projection of u0).
+// The uploads are asynchronous on the handle's stream (work enqueued on that
+// stream after them sees them).
 psd_status solve_prepare(psd_context* c, const double* f, const double* g, double* u) {
   TRY(ensure_fp64(c));
   if (c->prm.precision == PSD_MIXED) {
@@ -1075,16 +1085,28 @@ psd_status solve_prepare(psd_context* c, const double* f, const double* g, doubl
     Ctrl h3;
     init_ctrl(h3, -1.0, 1 << 30);
     h3.status = PSD_ERR_NOCONV;
-    TRY(upload_ctrl(c, c->ctrl3, h3));
+    TRY(upload_ctrl_async(c, c->ctrl3, h3, 1));
     Ctrl ht;
     inner_ctrl(c, ht, 0);
-    TRY(upload_ctrl(c, c->ctrl_tmpl, ht));
+    TRY(upload_ctrl_async(c, c->ctrl_tmpl, ht, 2));
   } else {
     Ctrl h;
     init_ctrl(h, c->prm.tol, c->prm.max_iter);
-    TRY(upload_ctrl(c, c->ctrl, h));
+    TRY(upload_ctrl_async(c, c->ctrl, h, 1));
   }
   (void)f;
+  return PSD_OK;
+}
+
+// Launch the handle's own solve graph (captured first if needed) on its
+// stream after solve_prepare; *ran false when graphs are off.
+psd_status solve_launch(psd_context* c, const double* f, const double* g, double* u, bool* ran) {
+  CK(cudaEventRecord(c->ev0, c->st));
+  if (c->prm.precision == PSD_MIXED)
+    TRY(launch_solve_graph(c, f, g, u, ran, [&]() { return mixed_graph_body(c, f, g, u); }));
+  else
+    TRY(launch_solve_graph(c, f, g, u, ran, [&]() { return fp64_graph_body(c, f, g, u); }));
+  CK(cudaEventRecord(c->ev1, c->st));
   return PSD_OK;
 }
 
@@ -1108,6 +1130,7 @@ psd_status solve_capture(psd_context* c, const double* f, const double* g, doubl
 // The statistics of a solve whose graph work has completed.
 psd_status solve_finish(psd_context* c, psd_info* info) {
   float ms = 0.f;
+  CK(cudaEventSynchronize(c->ev1));  // the solve may still run on its stream
   CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   if (c->prm.precision == PSD_MIXED) {
     Ctrl h3;
@@ -1282,7 +1305,7 @@ psd_status psd_create(const psd_params* params, psd_handle* out) {
     c->err = "cudaMemset failed";
     return bail(PSD_ERR_CUDA);
   }
-  if (cudaMallocHost((void**)&c->h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+  if (cudaMallocHost((void**)&c->h_ctrl, 4 * sizeof(Ctrl)) != cudaSuccess) {
     cudaGetLastError();
     c->err = "cudaMallocHost failed";
     return bail(PSD_ERR_NOMEM);
@@ -1879,6 +1902,9 @@ psd_status capture(psd_handle c, const double* f, const double* g, double* u, cu
   return solve_capture(c, f, g, u, st);
 }
 psd_status finish(psd_handle c, psd_info* info) { return solve_finish(c, info); }
+psd_status launch(psd_handle c, const double* f, const double* g, double* u, bool* ran) {
+  return solve_launch(c, f, g, u, ran);
+}
 cudaStream_t stream(psd_handle c) { return c->st; }
 psd_status tune(psd_handle c) { return autotune(c); }
 void set_error(psd_handle c, const char* msg) { c->err = msg; }

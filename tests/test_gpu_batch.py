@@ -40,6 +40,12 @@ def test_batch_matches_oracle_and_single_handle(oracle, precision):
     us = [torch.zeros(it["shape"], dtype=torch.float64, device="cuda") for it in insts]
     infos = B.solve([dev(f) for f in fs], us)
     assert B.mode() == 1  # one graph launch for the whole batch
+    for mode in (2, 3):  # the other schedules give the same bits
+        B.set_mode(mode)
+        us_m = [torch.zeros_like(u) for u in us]
+        B.solve([dev(f) for f in fs], us_m)
+        assert B.mode() == mode and all(torch.equal(a, b) for a, b in zip(us, us_m))
+    B.set_mode(0)
     for i, (it, f, u, info) in enumerate(zip(insts, fs, us, infos)):
         assert info["status"] == 0 and info["res_l2"] < tol
         P = oracle.Problem(4, it["h"], it["p"], it["s"], it["eps"])
@@ -47,6 +53,7 @@ def test_batch_matches_oracle_and_single_handle(oracle, precision):
         assert rel(u.cpu().numpy(), ref) <= (1e-11 if precision == PSD_FP64 else 1e-9), i
         S = Solver(4, it["shape"], it["h"], it["p"], it["s"], it["eps"], precision=precision, tol=tol,
                    max_iter=3000)
+        S.autotune()  # the batch tunes its mixed instances: same tiles, same reduction order
         u1 = torch.zeros_like(u)
         S.solve(dev(f), u1)
         assert torch.equal(u1, u), i
