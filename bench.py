@@ -35,6 +35,11 @@ import sys
 import tempfile
 import time
 
+# Up to 32 hardware work queues per process (the default is 8): the
+# batch's independent graph branches then run concurrently.  Read when
+# the CUDA context is created, so it is set before torch touches CUDA.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -238,16 +243,79 @@ def oracle_sample_all_cores(procs):
     return procs * SAMPLE_N ** 3 * SAMPLE_ITERS / wall, wall, [r[1] for r in res]
 
 
-def cpu_baseline_record():
-    """Single-thread and all-cores oracle throughput on this host."""
+def cpu_baseline_record(configs=False):
+    """Single-thread and all-cores oracle throughput on this host (and, with
+    configs, single-thread samples of the other workloads)."""
     v1, dt1 = oracle_sample()
     cores = host_cores()
     vall, wall, _ = oracle_sample_all_cores(cores)
     sample = (f"{SAMPLE_ITERS} PSD iterations of the same sixth-order problem (same parameters and field "
               f"recipe) on a {SAMPLE_N}^3 grid, numpy FP64; all cores: {cores} such samples as independent "
               f"processes at once ({wall:.1f} s wall); one core: one sample ({dt1:.1f} s)")
-    return {"value": vall, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-            "cpu_model": cpu_model(), "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "seconds": dt1}}
+    rec = {"value": vall, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+           "cpu_model": cpu_model(), "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "seconds": dt1}}
+    if configs:
+        rec["other_workloads_single_thread"] = oracle_config_samples()
+    return rec
+
+
+def oracle_config_samples():
+    """Single-thread CPU-oracle timings of the other workloads of the
+    benchmark family, each on a bounded sample stated in its entry (the
+    oracle as it stands, numpy FP64, one process)."""
+    import numpy as np
+
+    from oracle import psd_oracle as O
+    from paper_1607_01475_gb300 import synthetic
+
+    def problem(wl):
+        return O.Problem(wl["order"], wl["L"] / wl["shape"][-1], wl["p"], wl["s"], wl["eps"], wl.get("lam", 0.0))
+
+    def sample(wl, iters, tol=0.0):
+        P = problem(wl)
+        t0 = time.perf_counter()
+        u, info = O.psd_solve(P, wl["f"], wl["u0"], g=wl.get("g"), tol=tol, kmax=iters)
+        dt = time.perf_counter() - t0
+        cells = int(np.prod(wl["shape"]))
+        return u, info, dt, {"dof_iter_per_s": cells * info["iters"] / dt, "seconds": dt, "iters": info["iters"]}
+
+    out = {}
+    _, info, dt, rec = sample(synthetic.workload_small_2d(64), 1000, tol=TOL)
+    out["2d_64_fp64"] = dict(sample="the whole solve to ||r||_2 < 1e-10", time_to_tol_ms=1000 * dt,
+                             res_l2=info["res"][-1], **rec)
+    _, _, _, rec = sample(synthetic.workload_thin_film((1024, 1024)), 2)
+    out["2d_1024_thinfilm"] = dict(sample="2 PSD iterations of the 1024^2 workload", **rec)
+    _, _, _, rec = sample(synthetic.workload_thin_film((64, 64, 64)), 2)
+    out["3d_128_thinfilm"] = dict(sample="2 PSD iterations of the same recipe on 64^3 (one eighth of the "
+                                         "128^3 workload's cells)", **rec)
+    # the batch: 2 PSD iterations of the first instance of every grid size
+    wl = synthetic.workload_batch(96)
+    seen, cells, t = set(), 0, 0.0
+    for w in wl:
+        if w["shape"] in seen:
+            continue
+        seen.add(w["shape"])
+        one = dict(order=4, shape=w["shape"], L=w["L"], p=w["p"], s=w["s"], eps=w["eps"], f=w["f"],
+                   u0=np.zeros(w["shape"]))
+        _, info, dt, _ = sample(one, 2)
+        cells += int(np.prod(w["shape"])) * info["iters"]
+        t += dt
+    out["batch_96"] = dict(sample=f"2 PSD iterations of one instance of each grid size "
+                                  f"({', '.join(str(s_[0]) + '^2' for s_ in sorted(seen))})",
+                           dof_iter_per_s=cells / t, seconds=t)
+    # the adjoint on the 128^3 recipe at 32^3: forward solve, then PCG on the
+    # Hessian to 1e-12 relative
+    wl = synthetic.workload_thin_film((32, 32, 32))
+    P = problem(wl)
+    u, _ = O.psd_solve(P, wl["f"], wl["u0"], tol=TOL, kmax=1000)
+    h = wl["L"] / 32
+    ut = synthetic.fourier_field((32, 32, 32), wl["L"], 8, synthetic.seed_for(4, 0, 2))
+    t0 = time.perf_counter()
+    _, _, its = O.adjoint4(u, (u - ut) * h ** 3, P, tol=1e-12)
+    dt = time.perf_counter() - t0
+    out["adjoint_128"] = dict(sample="the adjoint of the same recipe at 32^3 (PCG to 1e-12 relative)",
+                              adjoint_ms=1000 * dt, cg_iters=its)
+    return out
 
 
 def run_reference(args):
@@ -393,7 +461,7 @@ def extra_workloads(args):
         brec[name] = {"batch_wall_ms": wall, "dof_iter_per_s": dofit / (wall / 1000.0),
                       "sum_instance_device_ms": sum(i["wall_ms"] for i in infos),
                       "all_converged": all(i["status"] == 0 for i in infos),
-                      "mode": "one graph launch" if B.mode() == 1 else "host threads"}
+                      "mode": {1: "one graph launch", 2: "per-instance graphs", 3: "host threads"}.get(B.mode())}
         B.close()
         del us
     out["batch_96"] = brec
@@ -584,7 +652,7 @@ def run_gpu(args):
     # -------- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_record()
+        cpu = cpu_baseline_record(configs=args.cpu_configs)
 
     # -------- the other workloads of the benchmark family, cuFFT comparison
     extra = None
@@ -628,6 +696,8 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads and the cuFFT comparison")
+    ap.add_argument("--cpu-configs", action="store_true",
+                    help="add single-thread oracle samples of the other workloads to cpu_baseline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

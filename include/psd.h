@@ -329,10 +329,15 @@ psd_status psd_noalloc_last_error(char* buf, size_t len);
  * graph launch: each instance's solve -- its loops are conditional WHILE
  * nodes driven by its device-resident stop flags -- is a branch of a single
  * graph captured on the first call (and again when a pointer changes), so
- * the instances' kernels overlap on the GPU with no host round trip.  When
- * a capture is not possible (kernel tracing on, or a capture failure) the
- * solves run from a pool of `workers` host threads (<= 0: min(count, 16)).
- * It synchronises the device before starting and returns when all
+ * the instances' kernels overlap on the GPU with no host round trip.  How
+ * many branches run at once is bounded by the process's hardware work
+ * queues: set CUDA_DEVICE_MAX_CONNECTIONS=32 in the environment before the
+ * CUDA context is created (the default, 8, leaves ~7 instances running at a
+ * time; on a GB300 the 96-instance 2D workload took 118 ms with 32 against
+ * 143 ms with 8).  When a capture is not possible (kernel tracing on, or a
+ * capture failure) each instance's own solve graph is launched on its
+ * stream instead; psd_batch_set_mode can also select a pool of `workers`
+ * host threads (<= 0: min(count, 16)).  It synchronises the device before starting and returns when all
  * instances are done; infos (host, count entries, may be NULL) receives
  * per-instance statistics (wall_ms: the instance's own span inside the
  * graph); the status is PSD_OK or the first failing instance's status
@@ -351,7 +356,7 @@ psd_status psd_batch_last_error(psd_batch b, char* buf, size_t len);
  * from the calling thread (no host round trip inside a solve); 3 = a pool
  * of host threads, one solve per thread at a time; 0 = the default (1).
  * PSD_ERR_INVALID for another value.  psd_batch_mode returns the schedule
- * the last solve used (a graph capture that fails falls back to 2 or 3;
+ * the last solve used (a graph capture that fails falls back to 2;
  * 0 = no solve yet or b NULL).                                             */
 psd_status psd_batch_set_mode(psd_batch b, int mode);
 int psd_batch_mode(psd_batch b);

@@ -11,9 +11,10 @@
 //
 // The graph is cached on the batch for the last set of f, g, u pointers.
 // When a capture is not possible (kernel tracing on an instance, or a
-// capture failure) the instances are solved as before the graph driver:
-// one host thread per instance at a time from a pool, the instances'
-// streams overlapping on the device.
+// capture failure) every instance's own solve graph is launched on its own
+// stream from this thread (or, for a handle whose graphs are off, its
+// direct loop runs); psd_batch_set_mode selects either of these schedules
+// or a pool of host threads explicitly.
 #include <cuda_runtime.h>
 
 #include <algorithm>
