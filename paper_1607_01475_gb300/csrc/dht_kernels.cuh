@@ -126,16 +126,33 @@ __global__ void __launch_bounds__(kThreads)
     vr[q] = valid ? to_compute<T>(s0[j + q * F::TS]) : T(0);
     vi[q] = valid ? to_compute<T>(s0[N + j + q * F::TS]) : T(0);
   }
-  F::run(vr, vi, j, sr, si, twc, tws);
-  if (valid) {
-    S* d0 = dst + (size_t)row0 * N;
+  if constexpr (F::TS <= 32 && !std::is_same<T, ff>::value) {
+    // a line's team is TS consecutive lanes: the last pass ends in registers
+    // and the Hartley split takes X[N - k] from the partner lane by shuffle
+    F::run_tw_regs(vr, vi, j, sr, si, TwPair<T>{twc, tws});
+    T h1[F::R], h2[F::R];
+    dht_split_regs<T, N, F::R, F::TS>(vr, vi, j, h1, h2);
+    if (valid) {
+      S* d0 = dst + (size_t)row0 * N;
 #pragma unroll
-    for (int q = 0; q < F::R; ++q) {
-      const int k = j + q * F::TS;
-      T h1, h2;
-      dht_split(sr, si, k, N, h1, h2);
-      d0[k] = to_storage<S>(scaled(h1, scale));
-      d0[N + k] = to_storage<S>(scaled(h2, scale));
+      for (int q = 0; q < F::R; ++q) {
+        const int k = j + q * F::TS;
+        d0[k] = to_storage<S>(scaled(h1[q], scale));
+        d0[N + k] = to_storage<S>(scaled(h2[q], scale));
+      }
+    }
+  } else {
+    F::run(vr, vi, j, sr, si, twc, tws);
+    if (valid) {
+      S* d0 = dst + (size_t)row0 * N;
+#pragma unroll
+      for (int q = 0; q < F::R; ++q) {
+        const int k = j + q * F::TS;
+        T h1, h2;
+        dht_split(sr, si, k, N, h1, h2);
+        d0[k] = to_storage<S>(scaled(h1, scale));
+        d0[N + k] = to_storage<S>(scaled(h2, scale));
+      }
     }
   }
 }

@@ -217,6 +217,80 @@ struct LineFFT {
     }
   }
 
+  // The last pass (NS * RP == N) with its results kept in registers: the
+  // butterfly b of this thread writes outputs jp + r NS = j + TS (b + M r),
+  // so after it the thread holds X[j + q TS] in vr[q] / vi[q] (q < R), the
+  // same points it loaded.
+  template <int NS, typename Tw>
+  __device__ __forceinline__ static void last_pass_regs(T (&vr)[R], T (&vi)[R], int j, const Tw& tw) {
+    constexpr int RP = N / NS;
+    constexpr int M = R / RP;
+    static_assert(RP * M == R, "last pass must cover the thread's points");
+    T outr[R], outi[R];
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const int jp = j + b * TS;  // < NS, so jp mod NS = jp
+      T xr[RP], xi[RP];
+#pragma unroll
+      for (int r = 0; r < RP; ++r) {
+        xr[r] = vr[b + r * M];
+        xi[r] = vi[b + r * M];
+      }
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < RP; ++r) {
+          T c, sn;
+          tw.get(jp * r, c, sn);
+          const T a = xr[r], bb = xi[r];
+          xr[r] = mul_add(bb, sn, a * c);
+          xi[r] = neg_mul_add(a, sn, bb * c);
+        }
+      }
+      DFT<RP>::run(xr, xi);
+#pragma unroll
+      for (int r = 0; r < RP; ++r) {
+        outr[b + M * r] = xr[r];
+        outi[b + M * r] = xi[r];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      vr[q] = outr[q];
+      vi[q] = outi[q];
+    }
+  }
+
+  template <int NS, typename Tw>
+  __device__ __forceinline__ static void rest_regs(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si, const Tw& tw) {
+    constexpr int RP = (N / NS >= R) ? R : N / NS;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      vr[q] = sr[pix(j + q * TS)];
+      vi[q] = si[pix(j + q * TS)];
+    }
+    if constexpr (NS * RP < N) {
+      __syncthreads();
+      pass<NS>(vr, vi, j, sr, si, tw);
+      rest_regs<NS * RP>(vr, vi, j, sr, si, tw);
+    } else {
+      last_pass_regs<NS>(vr, vi, j, tw);
+    }
+  }
+
+  // As run_tw, but the transform ends in registers (vr[q] / vi[q] = X[j + q
+  // TS]) instead of shared memory.  The line buffer is free on return only
+  // after a barrier.
+  template <typename Tw>
+  __device__ __forceinline__ static void run_tw_regs(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si, const Tw& tw) {
+    if constexpr (R == N) {
+      DFT<R>::run(vr, vi);  // one team thread holds the whole line
+    } else {
+      pass<1>(vr, vi, j, sr, si, tw);
+      rest_regs<R>(vr, vi, j, sr, si, tw);
+    }
+  }
+
   template <typename Tw>
   __device__ __forceinline__ static void run_tw(T (&vr)[R], T (&vi)[R], int j, T* sr, T* si, const Tw& tw) {
     pass<1>(vr, vi, j, sr, si, tw);
@@ -228,6 +302,34 @@ struct LineFFT {
     run_tw(vr, vi, j, sr, si, TwPair<T>{twc, tws});
   }
 };
+
+// Hartley outputs of the two real lines of a spectrum held in registers by
+// a team of TS <= 32 consecutive lanes (team thread j holds X[j + q TS] in
+// vr[q] / vi[q], as run_tw_regs leaves it): X[N - k] for k = j + q TS is
+// point R - 1 - q of team thread TS - j (j > 0), or this thread's own point
+// (R - q) mod R (j = 0), so one shuffle per value replaces the round trip
+// through shared memory.  Every thread of the block must call this (the
+// block is a power of two threads).
+template <typename T, int N, int R, int TS>
+__device__ __forceinline__ void dht_split_regs(const T (&vr)[R], const T (&vi)[R], int j, T (&h1)[R], T (&h2)[R]) {
+  static_assert(TS <= 32 && (TS & (TS - 1)) == 0 && TS * R == N, "team must fit in a warp");
+  const int lane = threadIdx.x & 31;
+  const int src = (lane & ~(TS - 1)) | ((TS - j) & (TS - 1));
+  // blocks are a power of two threads: whole warps, or one partial warp
+  const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : (1u << blockDim.x) - 1u;
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    T C = __shfl_sync(mask, vr[R - 1 - q], src);
+    T D = __shfl_sync(mask, vi[R - 1 - q], src);
+    if (j == 0) {
+      C = vr[(R - q) % R];
+      D = vi[(R - q) % R];
+    }
+    const T A = vr[q], B = vi[q];
+    h1[q] = half_of((A - B) + (C + D));
+    h2[q] = half_of((A + B) - (C - D));
+  }
+}
 
 // Hartley outputs of the two real lines packed in a complex spectrum (the
 // line stored with the padded index i + i/16).

@@ -245,6 +245,26 @@ __device__ __forceinline__ void gather_partials(A (&out)[M], const A* partials, 
   block_reduce<A, M, LASTMAX, ALLMAX>(out, sh);
 }
 
+// Tile order of the one-wave column march (residual and line-search
+// kernels).  The column-planes w = column * nz + z are split into G =
+// gridDim.x equal contiguous shares; the shares of CTAs b and b + G / g
+// (g = gcd(G, ncol)) start exactly ncol / g whole columns apart, so those
+// CTAs march the same plane at the same time.  The columns that agree
+// modulo m = ncol / g are therefore in lockstep, and they are given
+// consecutive tiles (whole rows of tiles when ncol / m is a multiple of the
+// row length): a tile's x-neighbours are then read in the same plane step,
+// and the halo reads they share hit L2 instead of DRAM.
+__device__ __forceinline__ int lockstep_classes(int G, int ncol) {
+  int a = G, b = ncol;
+  while (b != 0) {
+    const int t = a % b;
+    a = b;
+    b = t;
+  }
+  return ncol / a;
+}
+__device__ __forceinline__ int lockstep_tile(int col, int m, int ncol) { return (col % m) * (ncol / m) + col / m; }
+
 __device__ __forceinline__ int wrapi(int i, int n) {  // n a power of two
   return i & (n - 1);
 }

@@ -95,18 +95,22 @@ __global__ void __launch_bounds__(256, 2)
   }
   const T cbihq = FFX ? cbih * (T)fx_unit(fxs) : cbih;
 
-  // One wave of CTAs: the column-planes (w = column * nz + z, column = tile
-  // index, x fastest) are split into equal contiguous shares, each marched
-  // as one or more z-segments with their own prologue.
+  // One wave of CTAs: the column-planes (w = column * nz + z) are split
+  // into equal contiguous shares, each marched as one or more z-segments
+  // with their own prologue; columns map to tiles in lockstep order
+  // (lockstep_tile).
   const int gx = nx / TX;
-  const int wtot = gx * (ny / TY) * nz;
+  const int ncol = gx * (ny / TY);
+  const int wtot = ncol * nz;
   const int wend = (int)((long long)wtot * (blockIdx.x + 1) / gridDim.x);
+  const int mls = lockstep_classes(gridDim.x, ncol);
   T acc2 = T(0), accm = T(0);
   for (int w = (int)((long long)wtot * blockIdx.x / gridDim.x); w < wend;) {
     const int col = w / nz, z0 = w - col * nz;
     const int zc = min(nz - z0, wend - w);
     w += zc;
-    const int x0 = (col % gx) * TX, y0 = (col / gx) * TY;
+    const int tile = lockstep_tile(col, mls, ncol);
+    const int x0 = (tile % gx) * TX, y0 = (tile / gx) * TY;
 
     // this thread's U-tile elements (flattened e = tid, tid + 256) and where
     // they land in the halo-1 P/M tile
@@ -413,8 +417,10 @@ __global__ void __launch_bounds__(256, 3)
   // one wave of CTAs, each marching an equal share of the column-planes (as
   // the residual column kernel)
   const int gx = nx / TX;
-  const int wtot = gx * (ny / TY) * nz;
+  const int ncol = gx * (ny / TY);
+  const int wtot = ncol * nz;
   const int wend = (int)((long long)wtot * (blockIdx.x + 1) / gridDim.x);
+  const int mls = lockstep_classes(gridDim.x, ncol);
   int off[2], ely[2], elx[2];
   bool val[2];
 #pragma unroll
@@ -465,7 +471,8 @@ __global__ void __launch_bounds__(256, 3)
     const int col = w / nz, z0 = w - col * nz;
     const int zc = min(nz - z0, wend - w);
     w += zc;
-    const int x0 = (col % gx) * TX, y0 = (col / gx) * TY;
+    const int tile = lockstep_tile(col, mls, ncol);
+    const int x0 = (tile % gx) * TX, y0 = (tile / gx) * TY;
 #pragma unroll
     for (int k = 0; k < 2; ++k) off[k] = ((y0 + ely[k]) & (ny - 1)) * nx + ((x0 + elx[k]) & (nx - 1));
     fetch(z0);

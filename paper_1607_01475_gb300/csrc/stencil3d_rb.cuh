@@ -63,19 +63,22 @@ __global__ void __launch_bounds__(256, 2)
   const T beta = kconst<T>(kp).beta;
   const int cy0 = ty * NY;  // first own row (tile-local)
 
-  // The grid is one wave of CTAs.  The column-planes (w = column * nz + z,
-  // column = tile index, x fastest) are split into equal contiguous shares;
-  // a CTA marches its share as one or two z-segments, each with its own
-  // prologue, so no CTA waits for a second wave.
+  // The grid is one wave of CTAs.  The column-planes (w = column * nz + z)
+  // are split into equal contiguous shares; a CTA marches its share as one
+  // or two z-segments, each with its own prologue, so no CTA waits for a
+  // second wave.  Columns map to tiles in lockstep order (lockstep_tile).
   const int gx = nx / TX;
-  const int wtot = gx * (ny / TYT) * nz;
+  const int ncol = gx * (ny / TYT);
+  const int wtot = ncol * nz;
   const int wend = (int)((long long)wtot * (blockIdx.x + 1) / gridDim.x);
+  const int mls = lockstep_classes(gridDim.x, ncol);
   T acc2 = T(0), accm = T(0);
   for (int w = (int)((long long)wtot * blockIdx.x / gridDim.x); w < wend;) {
     const int col = w / nz, z0 = w - col * nz;
     const int zc = min(nz - z0, wend - w);
     w += zc;
-    const int x0 = (col % gx) * TX, y0 = (col / gx) * TYT;
+    const int tile = lockstep_tile(col, mls, ncol);
+    const int x0 = (tile % gx) * TX, y0 = (tile / gx) * TYT;
 
     // global offsets (within a plane) of the own cells
     int ooff[NY];
@@ -522,8 +525,10 @@ __global__ void __launch_bounds__(256, 3)
   // one wave of CTAs, each marching an equal share of the column-planes in
   // one or two z-segments (as the register-blocked residual)
   const int gx = nx / TX;
-  const int wtot = gx * (ny / TYT) * nz;
+  const int ncol = gx * (ny / TYT);
+  const int wtot = ncol * nz;
   const int wend = (int)((long long)wtot * (blockIdx.x + 1) / gridDim.x);
+  const int mls = lockstep_classes(gridDim.x, ncol);
   int x0 = 0, y0 = 0, ooff0 = 0, hoff = 0;
 
   // prefetched plane: u, base and d kept apart until the plane is used a
@@ -585,8 +590,9 @@ __global__ void __launch_bounds__(256, 3)
     const int col = w / nz, z0 = w - col * nz;
     const int zc = min(nz - z0, wend - w);
     w += zc;
-    x0 = (col % gx) * TX;
-    y0 = (col / gx) * TYT;
+    const int tile = lockstep_tile(col, mls, ncol);
+    x0 = (tile % gx) * TX;
+    y0 = (tile / gx) * TYT;
     ooff0 = (y0 + cy0) * nx + x0 + tx;  // own cell of row i: ooff0 + i nx
     hoff = ((y0 + hly) & (ny - 1)) * nx + ((x0 + hlx) & (nx - 1));
     fetch(z0);
