@@ -11,32 +11,40 @@
 namespace psd {
 namespace {
 
-// max |G|^2 over the vertices of an FP32 field (one vertex per thread,
-// grid-stride over the vertex planes; G from the 8 surrounding cells) into
-// ctrl->res_linf, and max |u| into ctrl->res_l2 (+inf if a value is not
-// finite).
+// max |G|^2 over the vertices of an FP32 field (G from the 8 surrounding
+// cells) into ctrl->res_linf, and max |u| into ctrl->res_l2 (+inf if a
+// value is not finite).  Each thread takes four consecutive vertices of a
+// row (x fastest, nx a multiple of 4, the field 16-byte aligned): the four
+// cell rows around them are read as float4 plus one scalar each.
 __global__ void __launch_bounds__(NT) k_gradmax(const float* __restrict__ u, KParams kp, Ctrl* ctrl,
                                                 double* partials) {
   __shared__ float sred[32 * 2];
   __shared__ int sflag;
   const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
-  const int lx = __ffs(nx) - 1, lxy = lx + __ffs(ny) - 1;  // sizes are powers of two
-  const size_t plane = (size_t)nx * ny, n = plane * nz;
+  const int lq = __ffs(nx / 4) - 1, lqy = lq + __ffs(ny) - 1;  // sizes are powers of two
+  const size_t plane = (size_t)nx * ny, nq = plane * nz / 4;
   float m = 0.0f, um = 0.0f;
-  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
-    const int x = (int)(i & (nx - 1)), y = (int)((i >> lx) & (ny - 1)), z = (int)(i >> lxy);
-    const int x1 = (x + 1) & (nx - 1), y1 = (y + 1) & (ny - 1), z1 = (z + 1) & (nz - 1);
-    const size_t r0 = (size_t)z * plane, r1 = (size_t)z1 * plane;
-    const float u000 = u[r0 + (size_t)y * nx + x], u001 = u[r0 + (size_t)y * nx + x1];
-    const float u010 = u[r0 + (size_t)y1 * nx + x], u011 = u[r0 + (size_t)y1 * nx + x1];
-    const float u100 = u[r1 + (size_t)y * nx + x], u101 = u[r1 + (size_t)y * nx + x1];
-    const float u110 = u[r1 + (size_t)y1 * nx + x], u111 = u[r1 + (size_t)y1 * nx + x1];
-    const float g0 = ((u001 - u000) + (u011 - u010)) + ((u101 - u100) + (u111 - u110));
-    const float g1 = ((u010 - u000) + (u011 - u001)) + ((u110 - u100) + (u111 - u101));
-    const float g2 = ((u100 - u000) + (u101 - u001)) + ((u110 - u010) + (u111 - u011));
-    m = fmaxf(m, g0 * g0 + g1 * g1 + g2 * g2);
-    const float au = fabsf(u000);
-    um = (au <= FLT_MAX) ? fmaxf(um, au) : INFINITY;  // NaN or infinity: +inf
+  for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < nq; i += (size_t)gridDim.x * NT) {
+    const int x = 4 * (int)(i & (nx / 4 - 1)), y = (int)((i >> lq) & (ny - 1)), z = (int)(i >> lqy);
+    const int x4 = (x + 4) & (nx - 1), y1 = (y + 1) & (ny - 1), z1 = (z + 1) & (nz - 1);
+    const float* r00 = u + (size_t)z * plane + (size_t)y * nx;  // rows (z, y), (z, y1), (z1, y), (z1, y1)
+    const float* r01 = u + (size_t)z * plane + (size_t)y1 * nx;
+    const float* r10 = u + (size_t)z1 * plane + (size_t)y * nx;
+    const float* r11 = u + (size_t)z1 * plane + (size_t)y1 * nx;
+    const float4 a = *reinterpret_cast<const float4*>(r00 + x), b = *reinterpret_cast<const float4*>(r01 + x);
+    const float4 c = *reinterpret_cast<const float4*>(r10 + x), d = *reinterpret_cast<const float4*>(r11 + x);
+    const float av[5] = {a.x, a.y, a.z, a.w, r00[x4]}, bv[5] = {b.x, b.y, b.z, b.w, r01[x4]};
+    const float cv[5] = {c.x, c.y, c.z, c.w, r10[x4]}, dv[5] = {d.x, d.y, d.z, d.w, r11[x4]};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // u000 = av[k], u001 = av[k+1] (x), u010 = bv[k] (y), u100 = cv[k] (z)
+      const float g0 = ((av[k + 1] - av[k]) + (bv[k + 1] - bv[k])) + ((cv[k + 1] - cv[k]) + (dv[k + 1] - dv[k]));
+      const float g1 = ((bv[k] - av[k]) + (bv[k + 1] - av[k + 1])) + ((dv[k] - cv[k]) + (dv[k + 1] - cv[k + 1]));
+      const float g2 = ((cv[k] - av[k]) + (cv[k + 1] - av[k + 1])) + ((dv[k] - bv[k]) + (dv[k + 1] - bv[k + 1]));
+      m = fmaxf(m, g0 * g0 + g1 * g1 + g2 * g2);
+      const float au = fabsf(av[k]);
+      um = (au <= FLT_MAX) ? fmaxf(um, au) : INFINITY;  // NaN or infinity: +inf
+    }
   }
   float v[2] = {m, um};
   block_reduce<float, 2, true, true>(v, sred);
@@ -125,43 +133,120 @@ __global__ void k_axpby(T* y, const T* x, const T* z, double a, double b, double
   }
 }
 
+// Element-wise helpers over whole fields.  Grids have an even number of
+// cells, so when the pointers are 16-byte aligned (always for the
+// handle's own buffers, not necessarily for a caller's) two elements move
+// per access; each thread keeps two such accesses in flight.
+__device__ __forceinline__ bool aligned16(const void* p) { return ((unsigned long long)p & 15ull) == 0; }
+
 // sum x, sum x^2, max |x| over n values -> ctrl (rd, res_l2 = sqrt(hd sum x^2), res_linf)
 __global__ void __launch_bounds__(NT) k_norms(const double* x, size_t n, double hd, Ctrl* c, double* partials) {
   __shared__ double sred[32 * 3];
   __shared__ int sflag;
-  double v[3] = {0.0, 0.0, -1.0};
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double t = x[i];
-    v[0] += t;
-    v[1] += t * t;
-    v[2] = fmax(v[2], fabs(t));
+  double v[3] = {0.0, 0.0, -1.0}, w[3] = {0.0, 0.0, -1.0};
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  auto add = [](double (&a)[3], double t) {
+    a[0] += t;
+    a[1] += t * t;
+    a[2] = fmax(a[2], fabs(t));
+  };
+  if (aligned16(x) && (n & 1) == 0) {
+    const double2* x2 = reinterpret_cast<const double2*>(x);
+    const size_t n2 = n / 2;
+    size_t i = t0;
+    for (; i + stride < n2; i += 2 * stride) {
+      const double2 a = x2[i], b = x2[i + stride];
+      add(v, a.x);
+      add(w, a.y);
+      add(v, b.x);
+      add(w, b.y);
+    }
+    if (i < n2) {
+      const double2 a = x2[i];
+      add(v, a.x);
+      add(w, a.y);
+    }
+  } else {
+    for (size_t i = t0; i < n; i += stride) add(v, x[i]);
   }
+  v[0] += w[0];
+  v[1] += w[1];
+  v[2] = fmax(v[2], w[2]);
   block_reduce<double, 3, true>(v, sred);
   if (publish_and_check_last<double>(v, 3, partials, &c->counter[CS_MISC], &sflag)) {
     double tt[3];
     gather_partials<double, 3, true>(tt, partials, sred);
-    double tot[3];
-    for (int m_ = 0; m_ < 3; ++m_) tot[m_] = (double)tt[m_];
     if (threadIdx.x == 0) {
-      c->rd = tot[0];
-      c->res_l2 = sqrt(hd * tot[1]);
-      c->res_linf = tot[2];
+      c->rd = tt[0];
+      c->res_l2 = sqrt(hd * tt[1]);
+      c->res_linf = tt[2];
       c->counter[CS_MISC] = 0;
     }
   }
 }
-__global__ void k_round_f32(float* out, const double* in, size_t n) {
+// The mean projection of order 6 on the device: c->c2 = mean(g - u), then
+// u += c->c2 (k_add_mean), with no host round trip.
+__global__ void __launch_bounds__(NT) k_mean_diff(const double* g, const double* u, size_t n, Ctrl* c,
+                                                  double* partials) {
+  __shared__ double sred[32];
+  __shared__ int sflag;
+  double v[1] = {0.0}, w = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    v[0] += g[i];
+    w += u[i];
+  }
+  v[0] -= w;
+  block_reduce<double, 1, false>(v, sred);
+  if (publish_and_check_last<double>(v, 1, partials, &c->counter[CS_MISC], &sflag)) {
+    double tt[1];
+    gather_partials<double, 1, false>(tt, partials, sred);
+    if (threadIdx.x == 0) {
+      c->c2 = tt[0] / (double)n;
+      c->counter[CS_MISC] = 0;
+    }
+  }
+}
+__global__ void k_add_mean(double* u, const Ctrl* c, size_t n) {
+  const double m = c->c2;
+  if (m == 0.0) return;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = (float)in[i];
+    u[i] += m;
+}
+__global__ void k_round_f32(float* out, const double* in, size_t n) {
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  if (aligned16(in) && aligned16(out) && (n & 1) == 0) {
+    const double2* in2 = reinterpret_cast<const double2*>(in);
+    float2* out2 = reinterpret_cast<float2*>(out);
+    for (size_t i = t0; i < n / 2; i += stride) {
+      const double2 a = in2[i];
+      out2[i] = make_float2((float)a.x, (float)a.y);
+    }
+  } else {
+    for (size_t i = t0; i < n; i += stride) out[i] = (float)in[i];
+  }
 }
 __global__ void k_accumulate_f64(double* u, const float* delta, float* u32, size_t n, const double* dsum,
                                  const int* skip) {
   if (skip != nullptr && *skip) return;
   const double m = dsum ? *dsum / (double)n : 0.0;  // mean of delta, removed
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = u[i] + ((double)delta[i] - m);
-    u[i] = v;
-    u32[i] = (float)v;
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  if (aligned16(u) && aligned16(delta) && aligned16(u32) && (n & 1) == 0) {
+    double2* u2 = reinterpret_cast<double2*>(u);
+    const float2* d2 = reinterpret_cast<const float2*>(delta);
+    float2* o2 = reinterpret_cast<float2*>(u32);
+    for (size_t i = t0; i < n / 2; i += stride) {
+      const double2 a = u2[i];
+      const float2 d = d2[i];
+      const double2 v = make_double2(a.x + ((double)d.x - m), a.y + ((double)d.y - m));
+      u2[i] = v;
+      o2[i] = make_float2((float)v.x, (float)v.y);
+    }
+  } else {
+    for (size_t i = t0; i < n; i += stride) {
+      const double v = u[i] + ((double)delta[i] - m);
+      u[i] = v;
+      u32[i] = (float)v;
+    }
   }
 }
 
@@ -440,7 +525,7 @@ cudaError_t launch_dot(const double* x, const double* y, const double* z, size_t
 }
 cudaError_t launch_gradmax(const float* u, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st) {
   const size_t n = (size_t)kp.nx * kp.ny * kp.nz;
-  k_gradmax<<<std::min(grid1d(n), 1024), NT, 0, st>>>(u, kp, ctrl, partials);
+  k_gradmax<<<std::min(grid1d(n / 4), 1024), NT, 0, st>>>(u, kp, ctrl, partials);  // 3D, nx % 4 == 0
   return cudaGetLastError();
 }
 cudaError_t launch_thinfilm_rhs(const double* u, double* f, const KParams& kp, cudaStream_t st) {
@@ -461,6 +546,11 @@ cudaError_t launch_energy_terms(const double* u, const double* f, double gbar, c
 }
 cudaError_t launch_norms(const double* x, size_t n, double hd, Ctrl* c, double* partials, cudaStream_t st) {
   k_norms<<<std::min(grid1d(n), 1024), NT, 0, st>>>(x, n, hd, c, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_mean_project(double* u, const double* g, size_t n, Ctrl* c, double* partials, cudaStream_t st) {
+  k_mean_diff<<<std::min(grid1d(n), 1024), NT, 0, st>>>(g, u, n, c, partials);
+  k_add_mean<<<grid1d(n), 256, 0, st>>>(u, c, n);
   return cudaGetLastError();
 }
 cudaError_t launch_round_f32(float* out, const double* in, size_t n, cudaStream_t st) {

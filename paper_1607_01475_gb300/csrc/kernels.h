@@ -191,6 +191,8 @@ cudaError_t launch_dot(const double* x, const double* y, const double* z, size_t
 // sum x -> c->rd, sqrt(hd sum x^2) -> c->res_l2, max|x| -> c->res_linf.
 cudaError_t launch_norms(const double* x, size_t n, double hd, Ctrl* c, double* partials, cudaStream_t st);
 // out = (float) in;  u += delta, u32 = (float) u  (mixed precision bookkeeping)
+// u += mean(g - u) (order 6 mean projection), the mean kept in c->c2.
+cudaError_t launch_mean_project(double* u, const double* g, size_t n, Ctrl* c, double* partials, cudaStream_t st);
 cudaError_t launch_round_f32(float* out, const double* in, size_t n, cudaStream_t st);
 // u += delta - mean(delta) (dsum: device pointer to sum(delta), or null for
 // no mean removal), u32 = (float) u.

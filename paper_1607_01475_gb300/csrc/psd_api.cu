@@ -825,19 +825,11 @@ void inner_ctrl(psd_context* c, Ctrl& h, int max_iter) {
   h.pre_stall_max = c->prm.inner_stall > 0 ? c->prm.inner_stall : kInnerStall;
 }
 
-// Order 6: the problem lives on mean(u) = mean(g); project u0 once (host).
+// Order 6: the problem lives on mean(u) = mean(g); project u0 once
+// (enqueued: the mean difference is formed and added on the device).
 psd_status mixed_project_mean(psd_context* c, const double* g, double* u) {
-  const KParams& kp = c->kp;
-  Ctrl hg, hu;
-  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(g, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
-  TRY(read_ctrl(c, c->ctrl2, hg));
-  { ProfScope p_(c, PSD_PROF_OTHER); CK(psd::launch_norms(u, c->N, kp.hd, c->ctrl2, c->partials, c->st)); }
-  TRY(read_ctrl(c, c->ctrl2, hu));
-  const double shift = (hg.rd - hu.rd) / (double)c->N;
-  if (shift != 0.0) {
-    ProfScope p_(c, PSD_PROF_OTHER);
-    CK(psd::launch_axpby<double>(u, u, nullptr, 1.0, 0.0, shift, c->N, c->st));
-  }
+  ProfScope p_(c, PSD_PROF_OTHER);
+  CK(psd::launch_mean_project(u, g, c->N, c->ctrl2, c->partials, c->st));
   return PSD_OK;
 }
 
