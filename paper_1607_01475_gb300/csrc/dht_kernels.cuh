@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kThreads)
     vr[q] = valid ? to_compute<T>(s0[j + q * F::TS]) : T(0);
     vi[q] = valid ? to_compute<T>(s0[N + j + q * F::TS]) : T(0);
   }
-  if constexpr (F::TS <= 32 && !std::is_same<T, ff>::value) {
+  if constexpr (F::TS <= 32) {
     // a line's team is TS consecutive lanes: the last pass ends in registers
     // and the Hartley split takes X[N - k] from the partner lane by shuffle
     F::run_tw_regs(vr, vi, j, sr, si, TwPair<T>{twc, tws});

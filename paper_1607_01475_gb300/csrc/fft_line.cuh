@@ -303,6 +303,17 @@ struct LineFFT {
   }
 };
 
+// Value of lane src of the same warp (float, double, or float-float as two
+// shuffles of its words).
+template <typename T>
+__device__ __forceinline__ T shfl_from(unsigned mask, T v, int src) {
+  return __shfl_sync(mask, v, src);
+}
+template <>
+__device__ __forceinline__ ff shfl_from<ff>(unsigned mask, ff v, int src) {
+  return ff(__shfl_sync(mask, v.hi, src), __shfl_sync(mask, v.lo, src));
+}
+
 // Hartley outputs of the two real lines of a spectrum held in registers by
 // a team of TS <= 32 consecutive lanes (team thread j holds X[j + q TS] in
 // vr[q] / vi[q], as run_tw_regs leaves it): X[N - k] for k = j + q TS is
@@ -319,8 +330,8 @@ __device__ __forceinline__ void dht_split_regs(const T (&vr)[R], const T (&vi)[R
   const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : (1u << blockDim.x) - 1u;
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    T C = __shfl_sync(mask, vr[R - 1 - q], src);
-    T D = __shfl_sync(mask, vi[R - 1 - q], src);
+    T C = shfl_from(mask, vr[R - 1 - q], src);
+    T D = shfl_from(mask, vi[R - 1 - q], src);
     if (j == 0) {
       C = vr[(R - q) % R];
       D = vi[(R - q) % R];
