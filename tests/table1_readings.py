@@ -19,6 +19,9 @@ Readings:
   T_0032        T = 0.032
   stable_sign   f = u + s Delta_h^v u (a decaying, non-physical sign)
   eps_0.2, eps_0.5   other eps
+  eps2_0.1      eps^2 = 0.1 (eps = 0.316); eps2_0.1_p6 the same at p = 6
+  s_coarse      both grids step with s = 0.1 h_c^2 (the coarse grid's h), T / s steps
+  s_fine        both grids step with s = 0.1 h_f^2 (the fine grid's h)
 """
 
 import argparse
@@ -41,6 +44,10 @@ READINGS = {
     "stable_sign": dict(explicit="plus"),
     "eps_0.2": dict(eps=0.2),
     "eps_0.5": dict(eps=0.5),
+    "eps2_0.1": dict(eps=float(np.sqrt(0.1))),
+    "eps2_0.1_p6": dict(eps=float(np.sqrt(0.1)), p=6.0),
+    "s_coarse": dict(s_from="coarse"),
+    "s_fine": dict(s_from="fine"),
 }
 
 
@@ -53,9 +60,10 @@ def init1(n, grid):
             - 0.1 * np.cos(2 * np.pi * (x - 2.0) / L) * np.sin(2 * np.pi * y / L))
 
 
-def run(n, p=4.0, T=0.32, eps=0.1, explicit="skew", grid="cell"):
+def run(n, p=4.0, T=0.32, eps=0.1, explicit="skew", grid="cell", s_h=None):
+    """s_h: the grid spacing that sets s = 0.1 s_h^2 (default: this grid's h)."""
     h = L / n
-    s = 0.1 * h * h
+    s = 0.1 * (s_h if s_h is not None else h) ** 2
     P = O.Problem(4, h, p, s, eps)
     u = init1(n, grid)
     for _ in range(int(round(T / s))):
@@ -91,12 +99,14 @@ def main():
     args = ap.parse_args()
     print("printed (p = 4): 16->32 6.2192e-3, 32->64 1.2685e-3")
     for name in args.reading:
-        cfg = READINGS[name]
+        cfg = dict(READINGS[name])
         grid = cfg.get("grid", "cell")
-        sols = {n: run(n, **cfg) for n in [16 * 2 ** k for k in range(args.pairs + 1)]}
+        s_from = cfg.pop("s_from", None)
         for k in range(args.pairs):
             nc = 16 * 2 ** k
-            d = sols[2 * nc] - up(sols[nc], grid)
+            s_h = None if s_from is None else L / (nc if s_from == "coarse" else 2 * nc)
+            uc, uf = run(nc, s_h=s_h, **cfg), run(2 * nc, s_h=s_h, **cfg)
+            d = uf - up(uc, grid)
             hf = L / (2 * nc)
             print(f"{name:14s} {nc:3d}->{2 * nc:3d}  l2 {np.sqrt(hf * hf * np.sum(d * d)):.4e}  "
                   f"rms {np.sqrt(np.mean(d * d)):.4e}  max {np.abs(d).max():.4e}", flush=True)
