@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads)
 // along the strided axis; thread (p, j) = (tid % pairs, tid / pairs) so that a
 // warp reads whole row segments.
 template <typename S, typename T, int N, int RM>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)  // FP32: 80 registers, 3 CTAs per SM
     k_dht_cols(S* data, size_t line_stride, size_t outer_stride, T scale, const int* done,
                const T* __restrict__ twc, const T* __restrict__ tws) {
   using F = LineFFT<T, N, RM>;
