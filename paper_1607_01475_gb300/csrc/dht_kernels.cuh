@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads)
 // along the strided axis; thread (p, j) = (tid % pairs, tid / pairs) so that a
 // warp reads whole row segments.
 template <typename S, typename T, int N, int RM>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)  // FP32: 80 registers, 3 CTAs per SM
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 || std::is_same<T, ff>::value ? 3 : 1)  // FP32 / float-float: 80 registers
     k_dht_cols(S* data, size_t line_stride, size_t outer_stride, T scale, const int* done,
                const T* __restrict__ twc, const T* __restrict__ tws) {
   using F = LineFFT<T, N, RM>;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)  // FP32: 80
 // (mean-zero projection).  Same thread mapping as k_dht_cols.
 enum { EPI_THETA = 0, EPI_RESID = 1 };
 template <int N, int RM, int EPI>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)  // 80 registers, 3 CTAs per SM
     k_dht_last_ff(const ff* data, double* theta, float* out32, size_t line_stride, size_t outer_stride,
                   KParams kp, Ctrl* ctrl, double* partials, const ff* __restrict__ twc,
                   const ff* __restrict__ tws, const ff* __restrict__ symx, const ff* __restrict__ symo,
