@@ -473,8 +473,13 @@ cudaError_t launch_residual(const ResArgs<T>& a, int mode, int pk, const KParams
 #undef PSD_RES_BY_PK
 }
 
-long long residual_grid_blocks(const KParams& kp, bool fp32) {
+ResGeom residual_geometry(const KParams& kp, bool fp32) {
   const ResGeom g = res_geometry(kp, fp32, 2);
+  return g.kind == RK_COL ? res_geometry(kp, fp32, 3) : g;
+}
+
+long long residual_grid_blocks(const KParams& kp, bool fp32) {
+  const ResGeom g = residual_geometry(kp, fp32);
   return (long long)g.grid.x * g.grid.y * g.grid.z;
 }
 

@@ -49,7 +49,7 @@ namespace {
 // selects it only when the worst-case float-float error of the flux part is
 // far below the solve tolerance (it scales with s q^4 max|G|^3).
 template <typename T, int PK, int MODE, bool FFX = false>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)  // 80 registers (FP64 fixed-point variant), 3 CTAs per SM
     k_res3d_col(ResArgs<T> a, KParams kp, Ctrl* ctrl, double* partials) {
   static_assert(!FFX || (sizeof(T) == 8 && MODE == RM_PLAIN && PK == PK_4), "FFX: FP64 plain p = 4 only");
   using FT = typename std::conditional<FFX, ff, T>::type;         // arithmetic type of the flux part

@@ -21,6 +21,8 @@ struct ResGeom {
 // Geometry for a kernel whose __launch_bounds__ guarantee ctas_per_sm
 // resident CTAs per SM (defined in k_stencil.cu).
 ResGeom res_geometry(const KParams& kp, bool fp32, int ctas_per_sm);
+// The residual launch: k_res3d_rb keeps 2 CTAs per SM resident, k_res3d_col 3.
+ResGeom residual_geometry(const KParams& kp, bool fp32);
 
 namespace detail {
 // Residual and line-search launchers for one vertex-factor kind PK (PK_4,

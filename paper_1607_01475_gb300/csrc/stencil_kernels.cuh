@@ -687,7 +687,7 @@ namespace detail {
 
 template <typename T, int PK, int MODE>
 cudaError_t res_impl(const ResArgs<T>& a, const KParams& kp, Ctrl* ctrl, double* partials, cudaStream_t st) {
-  const ResGeom g = res_geometry(kp, sizeof(T) == 4, 2);  // __launch_bounds__(256, 2)
+  const ResGeom g = residual_geometry(kp, sizeof(T) == 4);
   switch (g.kind) {
     case RK_RB4:
       if constexpr (sizeof(T) == 4) k_res3d_rb<T, PK, MODE, 4><<<g.grid, NT, 0, st>>>(a, kp, ctrl, partials);
