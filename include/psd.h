@@ -135,7 +135,13 @@ psd_status psd_precond_solve_f32(psd_handle h, const float* r, float* d);
  * is overwritten with the result.  w (order 6, may be NULL) receives
  * w = -T_h[u - g] + s lambda mean(g) - mean(f).  info (host, may be NULL)
  * receives the statistics.  Returns PSD_ERR_NOCONV if the tolerance was
- * not met within the iteration limits (u then holds the last iterate).     */
+ * not met within the iteration limits (u then holds the last iterate).
+ * The whole solve runs from one CUDA graph (loops as conditional WHILE
+ * nodes), captured on the first call with a given (u, f, g) and replayed
+ * afterwards; a handle keeps the graphs of its last four pointer sets, so a
+ * caller that alternates buffer sets (the next step's inputs copied in on
+ * another stream while this step is solved) replays without capturing.
+ * Returns when the solve is done (the handle's stream is synchronised).    */
 psd_status psd_solve(psd_handle h, const double* f, const double* g,
                      double* u, double* w, psd_info* info);
 

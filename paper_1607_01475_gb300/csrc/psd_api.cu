@@ -39,6 +39,7 @@ constexpr int kChunk = 8;          // iterations enqueued between host checks (d
 constexpr int kBody = 2;           // iterations per WHILE-loop body of a captured solve
 static_assert(kBody % 2 == 0, "a loop body must start and end on the same ping-pong parity");
 constexpr int kCapDepth = 3;       // nesting of WHILE loops: outer, inner, general-p line search
+constexpr int kSolveGraphs = 4;    // solve graphs cached per handle (by pointer set)
 static_assert(kChunk % 2 == 0, "a chunk must start and end on the same ping-pong parity");
 constexpr int kLsPassesGen = 16;   // Newton passes of the general-p line search
 constexpr double kInnerEta = 1e-4;  // inner FP32 solve: relative drop of the preconditioned norm
@@ -112,14 +113,22 @@ struct psd_context {
   std::vector<float> prof_durs[PSD_PROF_CLASSES];  // per-launch durations (ms)
 
   // The whole solve as one CUDA graph (its loops are WHILE conditional
-  // nodes), captured on private streams and replayed on st; keyed on the
-  // caller's u, f, g.
+  // nodes), captured on private streams and replayed on st.
   cudaStream_t gst = nullptr;
   cudaStream_t capst[kCapDepth] = {};
   int cap_depth = 0;
   bool capturing = false;
-  cudaGraphExec_t g_solve = nullptr;
-  const void* g_solve_key[3] = {nullptr, nullptr, nullptr};
+  // the last kSolveGraphs solve graphs by (u, f, g), least recently used
+  // replaced: a caller that alternates buffer sets (copies of the next
+  // step's inputs overlapping this step's solve) replays instead of
+  // capturing again
+  struct SolveGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void* key[3] = {nullptr, nullptr, nullptr};
+    unsigned long long used = 0;
+  };
+  SolveGraph g_solve[kSolveGraphs];
+  unsigned long long g_tick = 0;
   cudaGraphExec_t g_cg32 = nullptr;  // adjoint CG chunks: FP32 (mixed inner, own buffers)
   cudaGraphExec_t g_cg64 = nullptr;  // and FP64 (own buffers: u is copied in)
   bool graphs_off = false;  // a capture failed once: launch directly from then on
@@ -715,24 +724,31 @@ template <typename Enq>
 psd_status launch_solve_graph(psd_context* c, const double* f, const double* g, double* u, bool* ran, Enq&& enq) {
   *ran = false;
   if (c->prof || c->graphs_off) return PSD_OK;
-  if (c->g_solve && (c->g_solve_key[0] != u || c->g_solve_key[1] != f || c->g_solve_key[2] != g)) {
-    cudaGraphExecDestroy(c->g_solve);
-    c->g_solve = nullptr;
-  }
-  if (!c->g_solve) {
+  psd_context::SolveGraph* e = nullptr;
+  for (auto& x : c->g_solve)
+    if (x.exec && x.key[0] == u && x.key[1] == f && x.key[2] == g) e = &x;
+  if (!e) {
+    e = &c->g_solve[0];  // an empty slot, else the least recently used
+    for (auto& x : c->g_solve)
+      if (!x.exec || (e->exec && x.used < e->used)) e = &x;
+    if (e->exec) {
+      cudaGraphExecDestroy(e->exec);
+      e->exec = nullptr;
+    }
     c->capturing = true;
-    const psd_status s = capture_graph(c, &c->g_solve, enq);
+    const psd_status s = capture_graph(c, &e->exec, enq);
     c->capturing = false;
-    if (s != PSD_OK || !c->g_solve) {
+    if (s != PSD_OK || !e->exec) {
       c->graphs_off = true;
       c->err.clear();
       return PSD_OK;
     }
-    c->g_solve_key[0] = u;
-    c->g_solve_key[1] = f;
-    c->g_solve_key[2] = g;
+    e->key[0] = u;
+    e->key[1] = f;
+    e->key[2] = g;
   }
-  CK(cudaGraphLaunch(c->g_solve, c->st));
+  e->used = ++c->g_tick;
+  CK(cudaGraphLaunch(e->exec, c->st));
   *ran = true;
   return PSD_OK;
 }
@@ -1319,7 +1335,8 @@ psd_status psd_destroy(psd_handle c) {
                   c->adj_u, c->adj32[0], c->adj32[1]};
   for (void* p : ptrs) dev_free(c, p);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
-  if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
+  for (auto& x : c->g_solve)
+    if (x.exec) cudaGraphExecDestroy(x.exec);
   if (c->g_cg32) cudaGraphExecDestroy(c->g_cg32);
   if (c->g_cg64) cudaGraphExecDestroy(c->g_cg64);
   if (c->gst) cudaStreamDestroy(c->gst);
@@ -1488,10 +1505,11 @@ psd_status psd_autotune(psd_handle c, int* caps) {
   if (caps)
     for (int k = 0; k < 3; ++k) caps[k] = c->tb32.tile_cap[k];
   // captured solve graphs hold the old launch shapes
-  if (c->g_solve) {
-    cudaGraphExecDestroy(c->g_solve);
-    c->g_solve = nullptr;
-  }
+  for (auto& x : c->g_solve)
+    if (x.exec) {
+      cudaGraphExecDestroy(x.exec);
+      x.exec = nullptr;
+    }
   return PSD_OK;
 }
 
