@@ -52,3 +52,30 @@ def test_graph_solve_matches_host_driven_solve(shape, order, p, precision):
     assert (ig["iters"], ig["outer_iters"], ig["status"]) == (ih["iters"], ih["outer_iters"], ih["status"])
     assert ig["res_l2"] == ih["res_l2"]
     assert torch.equal(out["graph"][1], out["host"][1])
+
+
+@pytest.mark.parametrize("precision", [PSD_FP64, PSD_MIXED])
+def test_graph_cache_over_pointer_sets(precision):
+    """A handle keeps the solve graphs of its last four (u, f, g) pointer
+    sets: alternating two buffer sets, and cycling through six (more than
+    the cache holds, so graphs are replaced), every solve gives the answer
+    of a fresh handle bit for bit."""
+    shape, order = (32, 32, 32), 6
+    h = 2 * np.pi / shape[-1]
+    f = synthetic.fourier_field(shape, 2 * np.pi, 6, 21, nmodes=16)
+    g = synthetic.fourier_field(shape, 2 * np.pi, 6, 22, nmodes=16)
+    u0 = np.full(shape, g.mean())
+    kw = dict(precision=precision, tol=1e-10, max_iter=3000, max_outer=30)
+    ref = Solver(order, shape, h, 4.0, 0.05, 0.15, 1.0, **kw)
+    u_ref = dev(u0)
+    info_ref = ref.solve(dev(f), u_ref, dev(g))
+    ref.close()
+    S = Solver(order, shape, h, 4.0, 0.05, 0.15, 1.0, **kw)
+    sets = [(dev(f), dev(g), dev(u0)) for _ in range(6)]
+    for k in [0, 1, 0, 1, 2, 3, 4, 5, 0, 1, 5]:
+        fb, gb, ub = sets[k]
+        ub.copy_(dev(u0))
+        info = S.solve(fb, ub, gb)
+        assert info["iters"] == info_ref["iters"] and info["res_l2"] == info_ref["res_l2"]
+        assert torch.equal(ub, u_ref)
+    S.close()
