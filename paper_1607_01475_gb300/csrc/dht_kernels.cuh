@@ -602,11 +602,6 @@ __global__ void __launch_bounds__(256) k_spec_quad(const T* a, KParams kp, const
   }
 }
 
-__global__ void k_widen_f64(double* out, const float* in, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = (double)in[i];
-}
-
 template <typename T>
 __global__ void k_spec_apply_T(T* a, T scale, KParams kp, const T* sx, const T* sy, const T* sz, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {

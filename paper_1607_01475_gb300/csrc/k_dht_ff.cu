@@ -77,11 +77,6 @@ cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, cons
 }
 
 
-cudaError_t launch_widen_f64(double* out, const float* in, size_t n, cudaStream_t st) {
-  const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
-  k_widen_f64<<<grid, 256, 0, st>>>(out, in, n);
-  return cudaGetLastError();
-}
 
 
 void init_dht_attributes_f32();

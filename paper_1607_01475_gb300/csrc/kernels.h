@@ -63,8 +63,6 @@ cudaError_t launch_dht_last_ff(const ff* data, double* theta, float* out32, cons
 template <typename T>
 cudaError_t launch_mid(T* data, const KParams& kp, Ctrl* ctrl, double* partials, T* xi, T* dspec,
                        const AxisTables<T>& tb, cudaStream_t st);
-// out = (double) in, elementwise.
-cudaError_t launch_widen_f64(double* out, const float* in, size_t n, cudaStream_t st);
 
 // Spectral helpers (order 6, off the hot loop).
 // spec6_combine: a <- (mu == 0) ? 0 : a - b / mu   (a, b full DHT spectra)
