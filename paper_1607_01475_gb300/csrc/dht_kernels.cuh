@@ -408,7 +408,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 && ORDER == 4 && !PER
   V* pre_d = pre_x + (size_t)N * pairs;
   V* pre_w = pre_x + (ORDER == 6 ? 2 : 0) * (size_t)N * pairs;
   // element offsets in 32 bits: every grid has fewer than 2^32 cells
-  auto elem = [&](int q) { return (unsigned)(q * F::TS + j) * pairs + p; };
+  // staging index and line offset of the thread's q-th element; order 6
+  // forms them from per-thread offsets taken once (with the inline form the
+  // compiler spills there), order 4 keeps the inline form (no spill)
+  constexpr bool HOIST = ORDER == 6;
+  const unsigned e0 = (unsigned)j * pairs + p, estep = (unsigned)F::TS * pairs;
+  const unsigned jl = (unsigned)j * line_stride, ql = (unsigned)F::TS * line_stride;
+  auto elem = [&](int q) { return HOIST ? e0 + (unsigned)q * estep : (unsigned)(q * F::TS + j) * pairs + p; };
+  auto goff = [&](int q) { return HOIST ? jl + (unsigned)q * ql : (unsigned)(j + q * F::TS) * line_stride; };
   auto tile_base = [&](int t) {
     const int xb = t % ntx, yo = t / ntx;
     return (unsigned)yo * outer_stride + (unsigned)(xb * 2 * pairs + 2 * p);
@@ -426,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 && ORDER == 4 && !PER
   if (PERSIST && (int)blockIdx.x < ntiles) {
     const unsigned b0 = tile_base(blockIdx.x);
 #pragma unroll
-    for (int q = 0; q < F::R; ++q) copy_vec(pre_w + elem(q), data + (b0 + (unsigned)(j + q * F::TS) * line_stride));
+    for (int q = 0; q < F::R; ++q) copy_vec(pre_w + elem(q), data + (b0 + goff(q)));
     cp_async_commit();
   }
   int it = 0;
@@ -438,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 && ORDER == 4 && !PER
     if (ORDER == 6) {
 #pragma unroll
       for (int q = 0; q < F::R; ++q) {
-        const unsigned idx = base + (unsigned)(j + q * F::TS) * line_stride;
+        const unsigned idx = base + goff(q);
         copy_vec(pre_x + elem(q), xi + idx);
         copy_vec(pre_d + elem(q), dspec + idx);
       }
@@ -451,7 +458,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 && ORDER == 4 && !PER
         const unsigned bn = tile_base(tn);
         V* wnx = pre_w + (unsigned)((it + 1) & 1) * N * pairs;
 #pragma unroll
-        for (int q = 0; q < F::R; ++q) copy_vec(wnx + elem(q), data + (bn + (unsigned)(j + q * F::TS) * line_stride));
+        for (int q = 0; q < F::R; ++q) copy_vec(wnx + elem(q), data + (bn + goff(q)));
       }
       cp_async_commit();
       // this tile's data is the oldest group in flight
